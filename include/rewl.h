@@ -1,0 +1,251 @@
+/*
+ * rewl.h -- C ABI of the GB300 replica-exchange Wang-Landau (REWL) library.
+ *
+ * Method: Perera, Li, Eisenbach, Vogel, Landau, "Replica-exchange Wang-Landau sampling: pushing the
+ * limits of Monte Carlo simulations in materials sciences".  The library samples the density of
+ * states g(E) of the classical Heisenberg model H = -sum_{i<j} J_ij S_i.S_j, |S_i| = 1 (Sec. 3,
+ * Eq. 1) with many Wang-Landau walkers (Sec. 4.2, Eq. 4) in overlapping energy windows, replica
+ * exchange between adjacent windows (Sec. 4.3, Eq. 5) and joining of the ln g fragments where
+ * their slopes coincide (Sec. 4.3).  Thermodynamics follow from g(E) (Sec. 4.1, Eq. 2-3).
+ *
+ * Conventions (every entry point):
+ *   - A call returns rewl_status; REWL_OK is 0.  rewl_last_error() describes the latest failure
+ *     of a handle (or of handle-less calls when passed NULL).
+ *   - Inputs are copied at the call; the caller keeps ownership of its arrays.  Outputs go into
+ *     caller-allocated buffers whose sizes are stated per argument.
+ *   - Pointers documented as "host" must be host memory; "device" pointers must be device memory
+ *     of the current CUDA device.  Work is ordered on the handle's CUDA stream (rewl_config
+ *     .cuda_stream, NULL = legacy default stream); calls that return data to host memory
+ *     synchronise that stream before returning.
+ *   - Invalid arguments return REWL_EINVAL and leave the handle unchanged.  A CUDA failure
+ *     returns REWL_ECUDA; a handle that saw REWL_ECUDA must only be destroyed.
+ */
+#ifndef REWL_H
+#define REWL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rewl_handle rewl_handle; /* opaque, owned by the library */
+
+typedef enum {
+  REWL_OK = 0,
+  REWL_EINVAL = 1,   /* invalid argument or combination of arguments */
+  REWL_ENOMEM = 2,   /* host or device allocation failed */
+  REWL_ECUDA = 3,    /* a CUDA call failed */
+  REWL_ETIMEOUT = 4, /* a bounded device or host wait gave up (stage move cap, initial drive cap) */
+  REWL_ESTATE = 5    /* call not valid in the handle's current state */
+} rewl_status;
+
+enum {
+  REWL_LATTICE_BCC = 0,   /* periodic bcc, N = 2 L^3, neighbour shells 1..4 (Sec. 3) */
+  REWL_LATTICE_CHAIN = 1, /* open 1D chain of L spins, nearest neighbours only */
+  REWL_LATTICE_TABLE = 2  /* explicit neighbour table */
+};
+
+enum {
+  REWL_MODE_PRODUCTION = 0, /* FP32 spins and dE; ln g and energy in 64-bit fixed point */
+  REWL_MODE_TRAJECTORY = 1  /* everything FP64; reproduces the FP64 reference walk bit for bit */
+};
+
+/* Lattice.  bcc: site index 2 (x + L (y + L z)) + s for cubic cell (x, y, z), sublattice s (s = 1
+ * is the body centre).  Shell n (n = 1..4) holds the 8, 6, 12, 24 sites at squared distance 3/4,
+ * 1, 2, 11/4 (cubic lattice constant a = 1); periodic wrap needs every offset component < L/2.
+ * chain: site i couples to i-1 and i+1 with J[0]; the two ends have one neighbour.
+ * table: nbr[j * n_sites + i] is the j-th neighbour of site i (0 <= nbr < n_sites), J the
+ * coupling of that bond ([z][n_sites] both, row-major, copied); a coupling of 0 marks an unused slot;
+ * z <= 64. */
+typedef struct {
+  int32_t kind;
+  int32_t L;
+  int32_t n_sites, z;     /* table only */
+  const int32_t* nbr;     /* table only, host */
+  const double* J;        /* table only, host */
+} rewl_lattice;
+
+/* Couplings J_n of shell n for bcc (J > 0 ferromagnetic, H = -sum J S.S); J[0] for the chain. */
+typedef struct {
+  int32_t n_shells;
+  double J[4];
+} rewl_couplings;
+
+/* Energy range [e_min, e_max) split into n_bins bins of width (e_max - e_min) / n_bins, covered by
+ * n_windows windows (Sec. 3 restricted range; Sec. 4.3 windows).  e_min = e_max = NaN selects the
+ * default range: bcc [E_gs, 0] with E_gs the Luttinger-Tisza ground-state energy; chain the full
+ * range [-(L-1)|J|, (L-1)|J|].  Table lattices need an explicit range. */
+typedef struct {
+  double e_min, e_max;
+  int32_t n_bins, n_windows;
+} rewl_windows;
+
+typedef struct {
+  uint64_t seed;                 /* Philox key material */
+  int32_t mode;                  /* REWL_MODE_PRODUCTION or REWL_MODE_TRAJECTORY */
+  int32_t group_size;            /* lanes per trial move (1,2,4,8,16,32) = summation order of the
+                                    local field; 0 = choose from N and z */
+  int64_t exchange_interval;     /* trial moves per walker between replica exchanges (> 0) */
+  int64_t max_moves_per_stage;   /* cap for rewl_run_stage (moves per walker); 0 = no cap */
+  int64_t init_max_moves;        /* cap for the initial drive into the windows; 0 = 2^40 */
+  int32_t recompute_every;       /* production: full FP64 energy recomputation every this many
+                                    intervals (0 = every interval) */
+  int32_t reserved;
+  double lnf_initial;            /* initial ln f; 0 = 1 (f0 = e, Sec. 4.2) */
+  double timeout_s;              /* wall-clock cap for rewl_run_stage (0 = none) */
+  void* cuda_stream;             /* cudaStream_t used for every launch (NULL = default stream) */
+} rewl_config;
+
+typedef struct {
+  int64_t moves;               /* trial moves attempted in the call (all walkers) */
+  int64_t accepts;             /* accepted trial moves in the call */
+  int64_t exchange_attempts;   /* replica-exchange attempts in the call */
+  int64_t exchange_accepts;
+  int32_t intervals;           /* exchange intervals run */
+  int32_t n_halved;            /* ln f reductions in the call (all walkers) */
+  int32_t n_done;              /* walkers with ln f < lnf_final after the call */
+  int32_t all_done;            /* 1 when every walker has ln f < lnf_final */
+  double min_lnf, max_lnf;
+  double max_energy_drift;     /* largest |running E - recomputed E| seen so far */
+  double elapsed_ms;           /* wall time of the call */
+} rewl_stage_stats;
+
+typedef struct {
+  int32_t n_sites, z, n_slots, n_replicas;
+  int32_t n_bins, n_windows, walkers_per_window, window_bins;
+  int32_t group_size, mode;
+  double e_min, e_max, bin_width;
+  double initial_energy;       /* energy of the aligned starting state */
+  int64_t exchange_index;      /* replica-exchange rounds done */
+  int64_t intervals_done;
+  size_t shared_bytes_per_walker;
+  int32_t lattice_in_shared;   /* 1 when each walker's spins live in shared memory */
+  int32_t reserved;
+} rewl_info;
+
+typedef struct {
+  int64_t moves;
+  int64_t accepts;
+  int64_t recomputes;          /* trial moves whose dE was re-evaluated after an earlier accepted
+                                  move in the same batch touched its neighbourhood */
+} rewl_counters;
+
+/* Create a simulation: lattice and couplings (Sec. 3), windows (Sec. 4.3), m walkers per window,
+ * overlap o in [0, 1), flatness p in (0, 1) (Sec. 4.2), ln f_final > 0.  Builds the neighbour
+ * geometry, the window layout W = ceil(B / (1 + (h-1)(1-o))), start_k = round(k (B-W)/(h-1)),
+ * allocates device state and puts every replica in the aligned (+z) state.  Rejects: bad
+ * lattice (L too small for the shells, table index out of range), NaN couplings, empty or NaN
+ * energy range, h > B, W < 2, fewer than 2 overlap bins between adjacent windows, p or o out of
+ * range, lnf_final <= 0, exchange_interval < 1.  *out is NULL on failure. */
+rewl_status rewl_create(const rewl_lattice* lattice, const rewl_couplings* couplings,
+                        const rewl_windows* windows, int walkers_per_window, double overlap,
+                        double flatness, double lnf_final, const rewl_config* config,
+                        rewl_handle** out);
+
+/* Drive every walker from the aligned state into its window (the paper starts from an arbitrary
+ * configuration, Sec. 4.2): trial moves are accepted iff they do not increase the distance to the
+ * window centre; no ln g / H updates.  Called automatically by the first run call.
+ * REWL_ETIMEOUT if a walker needs more than init_max_moves. */
+rewl_status rewl_init_walkers(rewl_handle* h);
+
+/* Run n exchange intervals: each is exchange_interval Wang-Landau trial moves per walker (Sec. 4.2,
+ * Eq. 4; trial move Sec. 4.4) in one persistent launch, then the energy check/recomputation, one
+ * replica-exchange round (Sec. 4.3, Eq. 5) and the flatness check with ln f -> ln f / 2 (Sec. 4.2).
+ * stats may be NULL.  Stream-ordered; blocks only when stats is non-NULL. */
+rewl_status rewl_run_intervals(rewl_handle* h, int n_intervals, rewl_stage_stats* stats);
+
+/* Run intervals until every walker that had ln f >= ln f_final at the start of the call has reduced
+ * ln f at least once (one Wang-Landau iteration, Sec. 4.2), or until max_moves_per_stage / timeout_s.
+ * Returns REWL_ETIMEOUT when a cap ended the stage first.  stats may be NULL. */
+rewl_status rewl_run_stage(rewl_handle* h, rewl_stage_stats* stats);
+
+/* The three steps of one exchange interval as separate stream-ordered launches (for callers that
+ * interleave their own work or time each kernel): rewl_walk runs exchange_interval Wang-Landau
+ * trial moves per walker (Sec. 4.2, Eq. 4; Sec. 4.4) and the energy recomputation when due;
+ * rewl_flatness applies the flatness test and ln f -> ln f / 2 (Sec. 4.2).  Neither blocks. */
+rewl_status rewl_walk(rewl_handle* h);
+rewl_status rewl_flatness(rewl_handle* h);
+
+/* One replica-exchange round between adjacent windows (Sec. 4.3, Eq. 5): round t pairs windows
+ * (k, k+1), k = t mod 2 (step 2), walker a with walker (a + floor(t/2)) mod m; a swap needs both
+ * energies in the overlap and is accepted with min[1, g_i(E_A) g_j(E_B) / (g_i(E_B) g_j(E_A))]
+ * evaluated in FP64; an accepted swap exchanges the configurations' indices and energies, never
+ * the spins.  stats may be NULL (only the exchange fields are filled). */
+rewl_status rewl_exchange(rewl_handle* h, rewl_stage_stats* stats);
+
+/* Join the window fragments into ln g over all n_bins bins (Sec. 4.3): per window the m walkers are
+ * averaged after removing each one's mean; adjacent windows are joined at the interior overlap bin
+ * where their central-difference slopes differ least (lowest bin on ties); the result has mean 0.
+ * lng_out: host, [n_bins] FP64.  e_centres_out: host, [n_bins] bin-centre energies, may be NULL. */
+rewl_status rewl_merge_lng(rewl_handle* h, double* lng_out, double* e_centres_out);
+
+/* Same as rewl_merge_lng with the result left in device memory: lng_out_dev [n_bins] FP64, device. */
+rewl_status rewl_merge_lng_device(rewl_handle* h, double* lng_out_dev);
+
+/* Join given fragments (same rule as rewl_merge_lng), all device pointers: frag [h][m][W] FP64,
+ * starts [h] int32 (host), out [B] FP64 device.  bstar_out: device [h-1] int32, may be NULL.
+ * The windows must cover the bins: starts[0] = 0, starts[h-1] + W = n_bins, starts increasing with
+ * at least 2 overlap bins between neighbours (else REWL_EINVAL).  Scratch is allocated and freed on
+ * the stream (stream-ordered allocator); the call synchronises the stream before returning. */
+rewl_status rewl_stitch_device(const double* frag, const int32_t* starts_host, int n_windows,
+                               int walkers_per_window, int window_bins, int n_bins, double* out,
+                               int32_t* bstar_out, void* cuda_stream);
+
+/* Thermodynamics from ln g (Sec. 4.1, Eq. 2-3, k_B = 1): for every T, the mean energy U(T),
+ * the specific heat per spin C(T) = (<E^2> - <E>^2) / (N T^2) and ln Z(T).  All arrays host:
+ * lng, e_centres [n_bins]; T, U_out, C_out, lnZ_out [n_T] (outputs may be NULL). Computed on
+ * the device in FP64 on cuda_stream. */
+rewl_status rewl_thermo(const double* lng, const double* e_centres, int n_bins, double n_spins,
+                        const double* T, int n_T, double* U_out, double* C_out, double* lnZ_out,
+                        void* cuda_stream);
+
+/* Replace every walker's ln g by lng (host, [n_bins] over the global bins; each walker takes its
+ * window's slice) and set ln f = lnf0 (> 0) for all walkers; histograms are cleared. */
+rewl_status rewl_set_initial_lng(rewl_handle* h, const double* lng, double lnf0);
+
+/* Sizes and layout. */
+rewl_status rewl_get_info(const rewl_handle* h, rewl_info* out);
+
+/* Walker state, host arrays, any may be NULL: lng [S][W] FP64 (production converts from fixed
+ * point), H [S][W], E [S], bin [S] (global bin of E), lnf [S], replica [S] (configuration held by
+ * slot s = k m + a), stage [S] (ln f reductions), accepts [S], steps [S] (trial moves done),
+ * init_moves [S].  S = n_windows * walkers_per_window. */
+rewl_status rewl_get_walkers(rewl_handle* h, double* lng, uint32_t* H, double* E, int32_t* bin,
+                             double* lnf, int32_t* replica, int32_t* stage, int64_t* accepts,
+                             int64_t* steps, int64_t* init_moves);
+
+/* Spins of every configuration: host, [R][3][N] FP64 (x block, y block, z block). */
+rewl_status rewl_get_spins(rewl_handle* h, double* spins);
+
+/* Replica-exchange counters per window pair: host [n_windows - 1] each. */
+rewl_status rewl_get_exchange_counts(rewl_handle* h, int64_t* attempts, int64_t* accepts);
+
+/* Totals over all walkers. */
+rewl_status rewl_get_counters(rewl_handle* h, rewl_counters* out);
+
+/* The neighbour table as the device computes it: host [z][N] int32 and [z][N] FP64 couplings. */
+rewl_status rewl_get_neighbours(rewl_handle* h, int32_t* nbr, double* J);
+
+/* Full energy of every configuration recomputed on the device in FP64: host [R]. */
+rewl_status rewl_replica_energies(rewl_handle* h, double* E);
+
+/* Message for the latest failure of h (NULL: of the latest handle-less call). Never NULL. */
+const char* rewl_last_error(const rewl_handle* h);
+
+/* Release everything; NULL-safe. */
+void rewl_destroy(rewl_handle* h);
+
+/* Exp as used by the trajectory mode and the exchange acceptance, evaluated on the device for
+ * n host inputs (FP64): Cody-Waite reduction and a degree-13 Taylor polynomial.  For tests. */
+rewl_status rewl_device_exp(const double* x, double* y, int n);
+
+/* Measures this GPU's shared-memory load bandwidth (bytes/s) with a conflict-free 16-byte-load
+ * kernel on every SM; the peak the walker kernel's shared-memory traffic is compared against. */
+rewl_status rewl_measure_smem_bandwidth(double* bytes_per_s, double* ms, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,387 @@
+"""GB300 replica-exchange Wang-Landau (REWL) sampling for the classical Heisenberg model.
+
+Thin ctypes binding over ``librewl.so`` (C ABI in ``include/rewl.h``): argument marshalling only.
+Every step of the sampling runs in the library's CUDA kernels; there is no CPU fallback.  PyTorch,
+when present, supplies the CUDA stream (``torch.cuda.current_stream()``) and device buffers for the
+device-pointer entry points.
+
+Method: Perera, Li, Eisenbach, Vogel, Landau, "Replica-exchange Wang-Landau sampling: pushing the
+limits of Monte Carlo simulations in materials sciences" -- Heisenberg model on bcc (Sec. 3, Eq. 1),
+Wang-Landau walk (Sec. 4.2, Eq. 4), windows and replica exchange (Sec. 4.3, Eq. 5), joining of the
+ln g fragments (Sec. 4.3), thermodynamics from g(E) (Sec. 4.1, Eq. 2-3).
+"""
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+__all__ = ["REWL", "RewlError", "load_library", "thermo", "stitch_device", "device_exp",
+           "measure_smem_bandwidth", "BCC", "CHAIN", "TABLE", "PRODUCTION", "TRAJECTORY"]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librewl.so")
+
+BCC, CHAIN, TABLE = 0, 1, 2
+PRODUCTION, TRAJECTORY = 0, 1
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
+_STATUS = {0: "REWL_OK", 1: "REWL_EINVAL", 2: "REWL_ENOMEM", 3: "REWL_ECUDA", 4: "REWL_ETIMEOUT",
+           5: "REWL_ESTATE"}
+
+
+class RewlError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Lattice(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("L", C.c_int32), ("n_sites", C.c_int32), ("z", C.c_int32),
+                ("nbr", C.POINTER(C.c_int32)), ("J", C.POINTER(C.c_double))]
+
+
+class Couplings(C.Structure):
+    _fields_ = [("n_shells", C.c_int32), ("J", C.c_double * 4)]
+
+
+class Windows(C.Structure):
+    _fields_ = [("e_min", C.c_double), ("e_max", C.c_double), ("n_bins", C.c_int32),
+                ("n_windows", C.c_int32)]
+
+
+class Config(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("mode", C.c_int32), ("group_size", C.c_int32),
+                ("exchange_interval", C.c_int64), ("max_moves_per_stage", C.c_int64),
+                ("init_max_moves", C.c_int64), ("recompute_every", C.c_int32), ("reserved", C.c_int32),
+                ("lnf_initial", C.c_double), ("timeout_s", C.c_double), ("cuda_stream", C.c_void_p)]
+
+
+class StageStats(C.Structure):
+    _fields_ = [("moves", C.c_int64), ("accepts", C.c_int64), ("exchange_attempts", C.c_int64),
+                ("exchange_accepts", C.c_int64), ("intervals", C.c_int32), ("n_halved", C.c_int32),
+                ("n_done", C.c_int32), ("all_done", C.c_int32), ("min_lnf", C.c_double),
+                ("max_lnf", C.c_double), ("max_energy_drift", C.c_double), ("elapsed_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Info(C.Structure):
+    _fields_ = [("n_sites", C.c_int32), ("z", C.c_int32), ("n_slots", C.c_int32), ("n_replicas", C.c_int32),
+                ("n_bins", C.c_int32), ("n_windows", C.c_int32), ("walkers_per_window", C.c_int32),
+                ("window_bins", C.c_int32), ("group_size", C.c_int32), ("mode", C.c_int32),
+                ("e_min", C.c_double), ("e_max", C.c_double), ("bin_width", C.c_double),
+                ("initial_energy", C.c_double), ("exchange_index", C.c_int64), ("intervals_done", C.c_int64),
+                ("shared_bytes_per_walker", C.c_size_t), ("lattice_in_shared", C.c_int32),
+                ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class Counters(C.Structure):
+    _fields_ = [("moves", C.c_int64), ("accepts", C.c_int64), ("recomputes", C.c_int64)]
+
+
+_lib = None
+_vp = C.c_void_p
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def load_library(path=LIB_PATH):
+    """Load librewl.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = C.CDLL(path)
+    st = C.c_int
+    sig = {
+        "rewl_create": ([C.POINTER(Lattice), C.POINTER(Couplings), C.POINTER(Windows), C.c_int, C.c_double,
+                         C.c_double, C.c_double, C.POINTER(Config), C.POINTER(_vp)], st),
+        "rewl_init_walkers": ([_vp], st),
+        "rewl_run_intervals": ([_vp, C.c_int, C.POINTER(StageStats)], st),
+        "rewl_run_stage": ([_vp, C.POINTER(StageStats)], st),
+        "rewl_exchange": ([_vp, C.POINTER(StageStats)], st),
+        "rewl_walk": ([_vp], st),
+        "rewl_flatness": ([_vp], st),
+        "rewl_merge_lng": ([_vp, _vp, _vp], st),
+        "rewl_merge_lng_device": ([_vp, _vp], st),
+        "rewl_stitch_device": ([_vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp], st),
+        "rewl_thermo": ([_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, _vp, _vp, _vp], st),
+        "rewl_set_initial_lng": ([_vp, _vp, C.c_double], st),
+        "rewl_get_info": ([_vp, C.POINTER(Info)], st),
+        "rewl_get_walkers": ([_vp] + [_vp] * 10, st),
+        "rewl_get_spins": ([_vp, _vp], st),
+        "rewl_get_exchange_counts": ([_vp, _vp, _vp], st),
+        "rewl_get_counters": ([_vp, C.POINTER(Counters)], st),
+        "rewl_get_neighbours": ([_vp, _vp, _vp], st),
+        "rewl_replica_energies": ([_vp, _vp], st),
+        "rewl_last_error": ([_vp], C.c_char_p),
+        "rewl_destroy": ([_vp], None),
+        "rewl_device_exp": ([_vp, _vp, C.c_int], st),
+        "rewl_measure_smem_bandwidth": ([_vp, _vp, _vp], st),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(status, handle=None):
+    if status != OK:
+        msg = load_library().rewl_last_error(handle)
+        raise RewlError(status, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class REWL:
+    """One REWL simulation: h windows x m walkers over [e_min, e_max) in n_bins bins.
+
+    kind: BCC (L cells per side, couplings per shell J[0..3]), CHAIN (L spins, J[0]) or TABLE
+    (nbr, Jt arrays [z][n_sites]).  mode: PRODUCTION (FP32 spins, fixed-point ln g / energy) or
+    TRAJECTORY (FP64, bit-reproducible walk).
+    """
+
+    def __init__(self, kind=BCC, L=4, J=(1.0, 0.5), nbr=None, Jt=None, e_min=math.nan, e_max=math.nan,
+                 n_bins=200, n_windows=4, walkers_per_window=2, overlap=0.75, flatness=0.8,
+                 lnf_final=1e-3, seed=1, mode=PRODUCTION, group_size=0, exchange_interval=10000,
+                 max_moves_per_stage=0, init_max_moves=0, recompute_every=1, lnf_initial=0.0,
+                 timeout_s=0.0, stream=None):
+        lib = load_library()
+        lat = Lattice()
+        lat.kind = kind
+        lat.L = L
+        self._keep = []
+        if kind == TABLE:
+            nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+            Jt = np.ascontiguousarray(Jt, dtype=np.float64)
+            lat.z, lat.n_sites = nbr.shape
+            lat.nbr = nbr.ctypes.data_as(C.POINTER(C.c_int32))
+            lat.J = Jt.ctypes.data_as(C.POINTER(C.c_double))
+            self._keep += [nbr, Jt]
+        cp = Couplings()
+        J = list(J)
+        cp.n_shells = len(J)
+        for i in range(4):
+            cp.J[i] = J[i] if i < len(J) else 0.0
+        win = Windows()
+        win.e_min, win.e_max, win.n_bins, win.n_windows = e_min, e_max, n_bins, n_windows
+        cfg = Config()
+        cfg.seed = seed
+        cfg.mode = mode
+        cfg.group_size = group_size
+        cfg.exchange_interval = exchange_interval
+        cfg.max_moves_per_stage = max_moves_per_stage
+        cfg.init_max_moves = init_max_moves
+        cfg.recompute_every = recompute_every
+        cfg.lnf_initial = lnf_initial
+        cfg.timeout_s = timeout_s
+        cfg.cuda_stream = _stream_ptr(stream)
+        h = _vp()
+        _check(lib.rewl_create(C.byref(lat), C.byref(cp), C.byref(win), walkers_per_window, overlap, flatness,
+                               lnf_final, C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._lib = lib
+        info = self.info()
+        self.N, self.z = info["n_sites"], info["z"]
+        self.n_slots, self.B, self.h = info["n_slots"], info["n_bins"], info["n_windows"]
+        self.m, self.W = info["walkers_per_window"], info["window_bins"]
+        self.e_min, self.e_max, self.dE = info["e_min"], info["e_max"], info["bin_width"]
+        self.exchange_interval = exchange_interval
+        self.lnf_final = lnf_final
+        self.mode = mode
+
+    # -- lifecycle -------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rewl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- sampling --------------------------------------------------------------------------
+    def init_walkers(self):
+        _check(self._lib.rewl_init_walkers(self._h), self._h)
+
+    def run_intervals(self, n, stats=True):
+        s = StageStats() if stats else None
+        _check(self._lib.rewl_run_intervals(self._h, int(n), C.byref(s) if s is not None else None), self._h)
+        return s.as_dict() if s is not None else None
+
+    def run_stage(self):
+        s = StageStats()
+        st = self._lib.rewl_run_stage(self._h, C.byref(s))
+        if st not in (OK, ETIMEOUT):
+            _check(st, self._h)
+        d = s.as_dict()
+        d["capped"] = st == ETIMEOUT
+        return d
+
+    def exchange(self):
+        s = StageStats()
+        _check(self._lib.rewl_exchange(self._h, C.byref(s)), self._h)
+        return s.as_dict()
+
+    def walk(self):
+        """Enqueue one interval of trial moves (walker kernel only); does not block."""
+        _check(self._lib.rewl_walk(self._h), self._h)
+
+    def exchange_async(self):
+        """Enqueue one replica-exchange round; does not block."""
+        _check(self._lib.rewl_exchange(self._h, None), self._h)
+
+    def flatness(self):
+        """Enqueue the flatness test and ln f update; does not block."""
+        _check(self._lib.rewl_flatness(self._h), self._h)
+
+    def merge(self):
+        out = np.zeros(self.B)
+        cen = np.zeros(self.B)
+        _check(self._lib.rewl_merge_lng(self._h, _ptr(out), _ptr(cen)), self._h)
+        return out, cen
+
+    def merge_device(self, out):
+        """Merged ln g into a device buffer (e.g. a torch.float64 CUDA tensor of n_bins)."""
+        _check(self._lib.rewl_merge_lng_device(self._h, C.c_void_p(out.data_ptr())), self._h)
+        return out
+
+    def set_initial_lng(self, lng, lnf0):
+        lng = np.ascontiguousarray(lng, dtype=np.float64)
+        assert lng.size == self.B
+        _check(self._lib.rewl_set_initial_lng(self._h, _ptr(lng), float(lnf0)), self._h)
+
+    def run_to_convergence(self, max_stages=1000):
+        stages = []
+        for _ in range(max_stages):
+            st = self.run_stage()
+            stages.append(st)
+            if st["all_done"]:
+                break
+        return stages
+
+    # -- state -----------------------------------------------------------------------------
+    def info(self):
+        i = Info()
+        _check(self._lib.rewl_get_info(self._h, C.byref(i)), self._h)
+        return i.as_dict()
+
+    def walkers(self):
+        S, W = self.n_slots, self.W
+        out = dict(lng=np.zeros((S, W)), H=np.zeros((S, W), dtype=np.uint32), E=np.zeros(S),
+                   bin=np.zeros(S, dtype=np.int32), lnf=np.zeros(S), replica=np.zeros(S, dtype=np.int32),
+                   stage=np.zeros(S, dtype=np.int32), accepts=np.zeros(S, dtype=np.int64),
+                   steps=np.zeros(S, dtype=np.int64), init_moves=np.zeros(S, dtype=np.int64))
+        _check(self._lib.rewl_get_walkers(self._h, *[_ptr(out[k]) for k in
+                                                     ("lng", "H", "E", "bin", "lnf", "replica", "stage",
+                                                      "accepts", "steps", "init_moves")]), self._h)
+        return out
+
+    def spins(self):
+        sp = np.zeros((self.n_slots, 3, self.N))
+        _check(self._lib.rewl_get_spins(self._h, _ptr(sp)), self._h)
+        return sp
+
+    def exchange_counts(self):
+        n = max(self.h - 1, 1)
+        a = np.zeros(n, dtype=np.int64)
+        b = np.zeros(n, dtype=np.int64)
+        _check(self._lib.rewl_get_exchange_counts(self._h, _ptr(a), _ptr(b)), self._h)
+        return a[: self.h - 1], b[: self.h - 1]
+
+    def counters(self):
+        c = Counters()
+        _check(self._lib.rewl_get_counters(self._h, C.byref(c)), self._h)
+        return {"moves": c.moves, "accepts": c.accepts, "recomputes": c.recomputes}
+
+    def neighbours(self):
+        nbr = np.zeros((self.z, self.N), dtype=np.int32)
+        J = np.zeros((self.z, self.N))
+        _check(self._lib.rewl_get_neighbours(self._h, _ptr(nbr), _ptr(J)), self._h)
+        return nbr, J
+
+    def replica_energies(self):
+        E = np.zeros(self.n_slots)
+        _check(self._lib.rewl_replica_energies(self._h, _ptr(E)), self._h)
+        return E
+
+    def centres(self):
+        return self.e_min + (np.arange(self.B) + 0.5) * self.dE
+
+
+def thermo(lng, centres, n_spins, T, stream=None):
+    """(U(T), C(T)/N, ln Z(T)) from ln g at bin centres (k_B = 1), computed on the GPU."""
+    lib = load_library()
+    lng = np.ascontiguousarray(lng, dtype=np.float64)
+    centres = np.ascontiguousarray(centres, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    U, Cv, lnZ = np.zeros(T.size), np.zeros(T.size), np.zeros(T.size)
+    _check(lib.rewl_thermo(_ptr(lng), _ptr(centres), lng.size, float(n_spins), _ptr(T), T.size, _ptr(U),
+                           _ptr(Cv), _ptr(lnZ), _stream_ptr(stream)))
+    return U, Cv, lnZ
+
+
+def peak_temperature(T, Cv):
+    """Grid argmax of C(T) refined by a 3-point parabola (host arithmetic on the kernel's output)."""
+    i = int(np.argmax(Cv))
+    if i == 0 or i == len(T) - 1:
+        return float(T[i])
+    c0, c1, c2 = Cv[i - 1], Cv[i], Cv[i + 1]
+    den = c0 - 2 * c1 + c2
+    if den == 0:
+        return float(T[i])
+    return float(T[i] + 0.5 * (T[i + 1] - T[i]) * (c0 - c2) / den)
+
+
+def stitch_device(frag, starts, n_bins, out, bstar=None, stream=None):
+    """Join fragments frag [h][m][W] (float64 CUDA tensor) into out [n_bins] (float64 CUDA tensor)."""
+    lib = load_library()
+    h, m, W = frag.shape
+    st = np.ascontiguousarray(starts, dtype=np.int32)
+    _check(lib.rewl_stitch_device(C.c_void_p(frag.data_ptr()), _ptr(st), h, m, W, int(n_bins),
+                                  C.c_void_p(out.data_ptr()), None if bstar is None else C.c_void_p(bstar.data_ptr()),
+                                  _stream_ptr(stream)))
+    return out
+
+
+def device_exp(x):
+    lib = load_library()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros_like(x)
+    _check(lib.rewl_device_exp(_ptr(x), _ptr(y), x.size))
+    return y
+
+
+def measure_smem_bandwidth(stream=None):
+    lib = load_library()
+    bw = C.c_double()
+    ms = C.c_double()
+    _check(lib.rewl_measure_smem_bandwidth(C.byref(bw), C.byref(ms), _stream_ptr(stream)))
+    return bw.value, ms.value

@@ -1,0 +1,391 @@
+// kernels.cu -- replica exchange (Sec. 4.3, Eq. 5), flatness and ln f update (Sec. 4.2), joining
+// of the ln g fragments (Sec. 4.3), thermodynamics (Sec. 4.1, Eq. 2-3), and two measurement
+// kernels (device exp, shared-memory bandwidth).
+#include <cmath>
+
+#include "device_common.cuh"
+#include "walker.h"
+
+namespace rewl {
+
+// ------------------------------------------------------------------------------------------------
+// Replica exchange.  Round t pairs windows (k, k+1), k = t mod 2, t mod 2 + 2, ...; walker a of
+// window k meets walker (a + floor(t/2)) mod m of window k+1.  Slot i (window k) holds
+// configuration A, slot j (window k+1) holds B; the swap needs E_A in window k+1 and E_B in
+// window k and is accepted with min[1, exp(D)],
+//   D = ((ln g_i(E_A) - ln g_i(E_B)) + ln g_j(E_B)) - ln g_j(E_A)   (FP64),
+// u = u53(x0, x1) of Philox key (k, key1 ^ 0x5eed5eed), counter (t, 3, a).  Accepted swaps exchange
+// the configuration index and the energy; ln g and H stay with the slots.  One CTA, so the round
+// counter is read once and advanced after every pair is done.
+// ------------------------------------------------------------------------------------------------
+__global__ void exchange_kernel(const ExchangeArgs a) {
+  __shared__ long long t_s;
+  if (threadIdx.x == 0) t_s = *a.st.ex_index;
+  __syncthreads();
+  const long long t = t_s;
+  const int h = a.win.h, m = a.win.m, W = a.win.W;
+  const int parity = (int)(t & 1);
+  const int shift = (int)((unsigned long long)(t >> 1) % (unsigned long long)m);
+  const int total = ((h - parity) / 2) * m;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int k = parity + 2 * (idx / m);
+    const int aa = idx % m;
+    if (k + 1 >= h) continue;
+    const int i = k * m + aa;
+    const int j = (k + 1) * m + (aa + shift) % m;
+    const int si = a.win.starts[k], sj = a.win.starts[k + 1];
+    int bA, bB;
+    if (a.traj) {
+      bA = a.st.bin[i];
+      bB = a.st.bin[j];
+    } else {
+      bA = fx_bin(a.st.efx[i]);
+      bB = fx_bin(a.st.efx[j]);
+    }
+    atomicAdd(a.st.ex_att + k, 1ull);
+    if ((unsigned)(bA - sj) >= (unsigned)W || (unsigned)(bB - si) >= (unsigned)W) continue;
+    if ((unsigned)(bA - si) >= (unsigned)W || (unsigned)(bB - sj) >= (unsigned)W) continue;  // defensive
+    double D;
+    if (a.traj) {
+      const double* Li = a.st.lng + (size_t)i * W;
+      const double* Lj = a.st.lng + (size_t)j * W;
+      D = __dsub_rn(__dadd_rn(__dsub_rn(Li[bA - si], Li[bB - si]), Lj[bB - sj]), Lj[bA - sj]);
+    } else {
+      const long long* Li = a.st.lng_fx + (size_t)i * W;
+      const long long* Lj = a.st.lng_fx + (size_t)j * W;
+      const long long Dfx = ((Li[bA - si] - Li[bB - si]) + Lj[bB - sj]) - Lj[bA - sj];
+      D = __dmul_rn(__ll2double_rn(Dfx), kLngUnit);
+    }
+    bool accept = D >= 0.0;
+    if (!accept) {
+      const uint4 x = philox10(make_uint4((uint32_t)t, (uint32_t)((unsigned long long)t >> 32), 3u, (uint32_t)aa),
+                               make_uint2((uint32_t)k, a.key1 ^ 0x5eed5eedu));
+      accept = uniform53(x.x, x.y) < exp_fp64(D, a.ex);
+    }
+    if (accept) {
+      const int32_t tp = a.st.perm[i];
+      a.st.perm[i] = a.st.perm[j];
+      a.st.perm[j] = tp;
+      if (a.traj) {
+        const double te = a.st.E[i];
+        a.st.E[i] = a.st.E[j];
+        a.st.E[j] = te;
+        const int32_t tb = a.st.bin[i];
+        a.st.bin[i] = a.st.bin[j];
+        a.st.bin[j] = tb;
+      } else {
+        const long long te = a.st.efx[i];
+        a.st.efx[i] = a.st.efx[j];
+        a.st.efx[j] = te;
+      }
+      atomicAdd(a.st.ex_acc + k, 1ull);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *a.st.ex_index = t + 1;
+}
+
+cudaError_t launch_exchange(const ExchangeArgs& a, cudaStream_t stream) {
+  exchange_kernel<<<1, 256, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Flatness: a walker whose ln f is still >= ln f_final is flat when min H >= p * (sum H / W) over
+// the W bins of its window (and sum H > 0); then ln f -> ln f / 2, H -> 0, stage += 1.
+// One warp per walker.
+// ------------------------------------------------------------------------------------------------
+__global__ void flatness_kernel(const FlatnessArgs a) {
+  const int slot = blockIdx.x;
+  const int lane = threadIdx.x;
+  const int W = a.win.W;
+  bool active;
+  if (a.traj)
+    active = a.st.lnf[slot] >= a.lnf_final;
+  else
+    active = (double)a.st.lnf_fx[slot] * kLngUnit >= a.lnf_final;
+  if (!active) return;
+  uint32_t* H = a.st.H + (size_t)slot * W;
+  uint32_t mn = 0xffffffffu;
+  unsigned long long sum = 0;
+  for (int w = lane; w < W; w += 32) {
+    const uint32_t v = H[w];
+    mn = v < mn ? v : mn;
+    sum += v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t om = __shfl_xor_sync(kFullMask, mn, o);
+    mn = om < mn ? om : mn;
+    sum += __shfl_xor_sync(kFullMask, sum, o);
+  }
+  const double mean = __ddiv_rn(__ull2double_rn(sum), (double)W);
+  const bool flat = sum > 0 && __uint2double_rn(mn) >= __dmul_rn(a.flatness, mean);
+  if (!flat) return;
+  for (int w = lane; w < W; w += 32) H[w] = 0u;
+  if (lane == 0) {
+    if (a.traj) {
+      a.st.lnf[slot] = __dmul_rn(a.st.lnf[slot], 0.5);
+    } else {
+      const long long f = a.st.lnf_fx[slot] >> 1;
+      a.st.lnf_fx[slot] = f;
+      a.st.lnf[slot] = (double)f * kLngUnit;
+    }
+    a.st.stage[slot] += 1;
+  }
+}
+
+cudaError_t launch_flatness(const FlatnessArgs& a, int n_slots, cudaStream_t stream) {
+  flatness_kernel<<<n_slots, 32, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Joining the fragments.  Canonical 32-lane sum: lane l adds x[l], x[l+32], ... in order, then the
+// lanes combine with partners l^16 .. l^1 (every lane ends with the same value).
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ double frag_value(const MergeArgs& a, size_t idx) {
+  if (a.frag) return a.frag[idx];
+  return __dmul_rn(__ll2double_rn(a.frag_fx[idx]), kLngUnit);
+}
+
+__device__ double warp_sum32_frag(const MergeArgs& a, size_t base, int n) {
+  const int lane = threadIdx.x & 31;
+  double p = 0.0;
+  for (int i = lane; i < n; i += 32) p = __dadd_rn(p, frag_value(a, base + i));
+  for (int o = 16; o > 0; o >>= 1) p = __dadd_rn(p, __shfl_xor_sync(kFullMask, p, o));
+  return p;
+}
+
+__device__ double warp_sum32(const double* x, int n) {
+  const int lane = threadIdx.x & 31;
+  double p = 0.0;
+  for (int i = lane; i < n; i += 32) p = __dadd_rn(p, x[i]);
+  for (int o = 16; o > 0; o >>= 1) p = __dadd_rn(p, __shfl_xor_sync(kFullMask, p, o));
+  return p;
+}
+
+// (1) per window k: A_k[w] = (sum_a (x_a[w] - mean_a)) / m, mean_a = sum32(x_a) / W.
+__global__ void merge_avg_kernel(const MergeArgs a) {
+  extern __shared__ double means[];
+  const int k = blockIdx.x;
+  const int W = a.W, m = a.m;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int w = warp; w < m; w += nw) {
+    const double s = warp_sum32_frag(a, ((size_t)k * m + w) * W, W);
+    if ((threadIdx.x & 31) == 0) means[w] = __ddiv_rn(s, (double)W);
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    double t = 0.0;
+    for (int aa = 0; aa < m; ++aa) t = __dadd_rn(t, __dsub_rn(frag_value(a, ((size_t)k * m + aa) * W + w), means[aa]));
+    a.avg[(size_t)k * W + w] = __ddiv_rn(t, (double)m);
+  }
+}
+
+// (2)-(4) join points, shifts, assembly, mean removal.  One CTA.
+__global__ void merge_join_kernel(const MergeArgs a) {
+  extern __shared__ unsigned char js[];
+  double* shift = reinterpret_cast<double*>(js);
+  int* bst = reinterpret_cast<int*>(shift + a.h);
+  __shared__ double mean_s;
+  const int h = a.h, W = a.W, B = a.B;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  for (int k = warp; k + 1 < h; k += nw) {
+    const int sk = a.starts[k], sn = a.starts[k + 1];
+    const int lo = sn + 1, hi = sk + W - 2;
+    const double* Ak = a.avg + (size_t)k * W;
+    const double* An = a.avg + (size_t)(k + 1) * W;
+    double bv = inf;
+    int bb = -1;
+    for (int b = lo + lane; b <= hi; b += 32) {
+      const double s1 = __dsub_rn(Ak[b + 1 - sk], Ak[b - 1 - sk]);
+      const double s2 = __dsub_rn(An[b + 1 - sn], An[b - 1 - sn]);
+      const double v = fabs(__dsub_rn(s1, s2));
+      if (v < bv) {            // lanes visit b in increasing order: first minimum kept
+        bv = v;
+        bb = b;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(kFullMask, bv, o);
+      const int ob = __shfl_xor_sync(kFullMask, bb, o);
+      if (ob >= 0 && (bb < 0 || ov < bv || (ov == bv && ob < bb))) {
+        bv = ov;
+        bb = ob;
+      }
+    }
+    if (lane == 0) bst[k] = bb >= 0 ? bb : sn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    shift[0] = 0.0;
+    for (int k = 0; k + 1 < h; ++k) {
+      const int b = bst[k];
+      shift[k + 1] = __dadd_rn(shift[k], __dsub_rn(a.avg[(size_t)k * W + (b - a.starts[k])],
+                                                   a.avg[(size_t)(k + 1) * W + (b - a.starts[k + 1])]));
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    int k = 0;
+    while (k + 1 < h && b >= bst[k]) ++k;
+    a.out[b] = __dadd_rn(a.avg[(size_t)k * W + (b - a.starts[k])], shift[k]);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const double s = warp_sum32(a.out, B);
+    if (lane == 0) mean_s = __ddiv_rn(s, (double)B);
+  }
+  __syncthreads();
+  const double mu = mean_s;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) a.out[b] = __dsub_rn(a.out[b], mu);
+  if (a.bstar)
+    for (int k = threadIdx.x; k + 1 < h; k += blockDim.x) a.bstar[k] = bst[k];
+}
+
+cudaError_t launch_merge(const MergeArgs& a, cudaStream_t stream) {
+  merge_avg_kernel<<<a.h, 256, sizeof(double) * (size_t)a.m, stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t js = sizeof(double) * (size_t)a.h + sizeof(int) * (size_t)a.h;
+  if (js > 48 * 1024) {
+    e = cudaFuncSetAttribute(merge_join_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)js);
+    if (e != cudaSuccess) return e;
+  }
+  merge_join_kernel<<<1, 1024, js, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Thermodynamics (k_B = 1): w_b = exp(ln g_b - E_b / T - max), Z = sum w, U = sum w E / Z,
+// var = sum w (E - U)^2 / Z (two passes), C/N = var / (N T^2), ln Z = max + ln(sum w).
+// One CTA per temperature.
+// ------------------------------------------------------------------------------------------------
+__device__ double block_reduce(double v, double* red, bool is_max) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(kFullMask, v, o);
+    v = is_max ? fmax(v, ov) : v + ov;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double x = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : (is_max ? -1e308 : 0.0);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ox = __shfl_xor_sync(kFullMask, x, o);
+      x = is_max ? fmax(x, ox) : x + ox;
+    }
+    if (threadIdx.x == 0) red[32] = x;
+  }
+  __syncthreads();
+  const double r = red[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void thermo_kernel(const double* lng, const double* E, int B, double n_spins, const double* T,
+                              double* U, double* C, double* lnZ) {
+  __shared__ double red[33];
+  const double t = T[blockIdx.x];
+  const double beta = 1.0 / t;
+  double mx = -1e308;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) mx = fmax(mx, lng[b] - E[b] * beta);
+  mx = block_reduce(mx, red, true);
+  double z = 0.0, e1 = 0.0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const double w = exp(lng[b] - E[b] * beta - mx);
+    z += w;
+    e1 += w * E[b];
+  }
+  z = block_reduce(z, red, false);
+  e1 = block_reduce(e1, red, false);
+  const double u = e1 / z;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const double w = exp(lng[b] - E[b] * beta - mx);
+    const double d = E[b] - u;
+    v += w * d * d;
+  }
+  v = block_reduce(v, red, false) / z;
+  if (threadIdx.x == 0) {
+    if (U) U[blockIdx.x] = u;
+    if (C) C[blockIdx.x] = v * beta * beta / n_spins;
+    if (lnZ) lnZ[blockIdx.x] = mx + log(z);
+  }
+}
+
+cudaError_t launch_thermo(const double* lng, const double* E, int B, double n_spins, const double* T, int nT,
+                          double* U, double* C, double* lnZ, cudaStream_t stream) {
+  thermo_kernel<<<nT, 256, 0, stream>>>(lng, E, B, n_spins, T, U, C, lnZ);
+  return cudaGetLastError();
+}
+
+__global__ void device_exp_kernel(const double* x, double* y, int n, const ExpCoeffs c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = exp_fp64(x[i], c);
+}
+
+cudaError_t launch_device_exp(const double* x, double* y, int n, const ExpCoeffs& c, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  device_exp_kernel<<<(n + 255) / 256, 256, 0, stream>>>(x, y, n, c);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Shared-memory load bandwidth: every thread reads 16-byte words of a 48 KB buffer so that each
+// quarter-warp covers all 32 banks once (conflict free).  Index always inside the buffer.
+// ------------------------------------------------------------------------------------------------
+constexpr int kBwWords = 3072;   // float4 words = 48 KB
+
+__global__ void smem_bw_kernel(float* out, int iters) {
+  __shared__ float4 buf[kBwWords];
+  for (int i = threadIdx.x; i < kBwWords; i += blockDim.x) buf[i] = make_float4((float)i, 1.f, 2.f, 3.f);
+  __syncthreads();
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float4 v = buf[(threadIdx.x + u * 256 + (it & 1) * 1024) % kBwWords];
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = acc.x + acc.y + acc.z + acc.w;
+}
+
+cudaError_t measure_smem_bandwidth(double* bytes_per_s, double* ms_out, cudaStream_t stream) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int blocks = nsm * 4, threads = 256, iters = 4096;
+  float* out = nullptr;
+  e = cudaMallocAsync(&out, sizeof(float) * (size_t)blocks * threads, stream);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, stream);
+    smem_bw_kernel<<<blocks, threads, 0, stream>>>(out, iters);
+    cudaEventRecord(e1, stream);
+    e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(out, stream);
+  if (e != cudaSuccess) return e;
+  const double bytes = (double)blocks * threads * iters * 8 * 16;
+  *bytes_per_s = bytes / (best * 1e-3);
+  if (ms_out) *ms_out = best;
+  return cudaGetLastError();
+}
+
+}  // namespace rewl

@@ -1,0 +1,78 @@
+// rewl_types.h -- plain structs passed by value to the REWL kernels (host and device side).
+#pragma once
+
+#include <cstdint>
+
+namespace rewl {
+
+constexpr int kMaxSlotsPerSite = 64;   // neighbour slots z
+constexpr int kWalkerThreads = 128;    // threads per walker CTA (warp 0 walks; all load/store)
+
+struct ExpCoeffs {
+  double inv_fact[14];                 // 1/n!, n = 0..13, each c[n] = c[n-1] / n in IEEE FP64
+};
+
+struct Geometry {
+  int kind;                            // 0 bcc (arithmetic neighbours), 1 table
+  int N, z, L;
+  uint32_t divL;                       // ceil(2^32 / L) for bcc
+  int r2max;                           // bcc: largest squared half-unit offset of the shells
+  uint32_t off[kMaxSlotsPerSite];      // bcc: packed offsets (see unpack_offset)
+  float Jf[kMaxSlotsPerSite];          // bcc: coupling per slot
+  double Jd[kMaxSlotsPerSite];
+  int n_energy_slots;                  // slots summed by the energy recomputation
+  float energy_weight;                 // 1 (bcc, forward half of every shell) or 0.5 (table, all)
+  uint8_t energy_slot[kMaxSlotsPerSite];
+  const int32_t* tab_nbr;              // table: [z][N]
+  const float* tab_Jf;                 // table: [z][N]
+  const double* tab_Jd;                // table: [z][N]
+};
+
+struct Windows {
+  int B, h, m, W;
+  const int32_t* starts;               // [h]
+  double e_min, dE;                    // bin b covers [e_min + b dE, e_min + (b+1) dE)
+  float dq_scale;                      // 2^32 / dE (production energy increments)
+};
+
+struct WalkerState {
+  void* spins;                         // [R][3][N] float (production) or double (trajectory)
+  int32_t* perm;                       // [S] configuration held by slot s
+  uint32_t* H;                         // [S][W]
+  long long* lng_fx;                   // production [S][W], 2^-40 units
+  long long* efx;                      // production [S], 2^-32 bins above e_min
+  long long* lnf_fx;                   // production [S]
+  double* lng;                         // trajectory [S][W]
+  double* E;                           // trajectory [S]
+  int32_t* bin;                        // trajectory [S]
+  double* lnf;                         // [S] (production keeps it equal to lnf_fx * 2^-40)
+  int32_t* stage;                      // [S]
+  long long* steps;                    // [S] Wang-Landau trial moves done
+  long long* accepts;                  // [S]
+  long long* recomputes;               // [S]
+  long long* init_moves;               // [S]
+  double* drift;                       // [S] largest |running E - recomputed E|
+  int32_t* ctrl;                       // [0] error code, [1] halved counter, [2] done counter
+  long long* ex_index;                 // replica-exchange rounds done (device counter)
+  unsigned long long* ex_att;          // [h-1]
+  unsigned long long* ex_acc;          // [h-1]
+};
+
+struct WalkerArgs {
+  Geometry geo;
+  Windows win;
+  WalkerState st;
+  ExpCoeffs ex;
+  long long moves;                     // trial moves per walker in this launch
+  long long init_cap;                  // cap of the initial drive
+  uint32_t key1;                       // seed_lo ^ seed_hi
+  int G;                               // lanes per trial move
+  int init;                            // 1: initial drive into the windows
+  int recompute;                       // 1: energy recomputation at the end of the launch
+  double lnf_final;
+};
+
+// error codes written to ctrl[0]
+enum : int32_t { kErrNone = 0, kErrInitCap = 1, kErrOutOfWindow = 2 };
+
+}  // namespace rewl

@@ -1,0 +1,55 @@
+// walker.h -- host-side launchers of the REWL kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rewl_types.h"
+
+namespace rewl {
+
+size_t walker_smem_bytes(bool traj, bool smem_lattice, int N, int W);
+cudaError_t launch_walkers(const WalkerArgs& a, int n_slots, bool traj, bool smem_lattice, size_t smem,
+                           cudaStream_t stream);
+
+struct ExchangeArgs {
+  Windows win;
+  WalkerState st;
+  ExpCoeffs ex;
+  uint32_t key1;
+  int traj;
+};
+cudaError_t launch_exchange(const ExchangeArgs& a, cudaStream_t stream);
+
+struct FlatnessArgs {
+  Windows win;
+  WalkerState st;
+  double flatness;
+  double lnf_final;
+  int traj;
+};
+cudaError_t launch_flatness(const FlatnessArgs& a, int n_slots, cudaStream_t stream);
+
+// Merge: fragments are read from either an FP64 array or a 2^-40 fixed-point array [h][m][W].
+struct MergeArgs {
+  const double* frag;
+  const long long* frag_fx;
+  const int32_t* starts;     // device [h]
+  int h, m, W, B;
+  double* avg;               // scratch [h][W]
+  int32_t* bstar;            // scratch or output [h-1] (may be null only when h == 1)
+  double* out;               // [B]
+};
+cudaError_t launch_merge(const MergeArgs& a, cudaStream_t stream);
+
+cudaError_t launch_thermo(const double* lng, const double* E, int B, double n_spins, const double* T, int nT,
+                          double* U, double* C, double* lnZ, cudaStream_t stream);
+
+cudaError_t launch_device_exp(const double* x, double* y, int n, const ExpCoeffs& c, cudaStream_t stream);
+
+cudaError_t launch_energies(const WalkerArgs& a, int n_replicas, bool traj, double* out, cudaStream_t stream);
+
+cudaError_t launch_neighbour_dump(const Geometry& g, int32_t* nbr, double* J, cudaStream_t stream);
+
+cudaError_t measure_smem_bandwidth(double* bytes_per_s, double* ms, cudaStream_t stream);
+
+}  // namespace rewl

@@ -1,0 +1,121 @@
+"""Trajectory-mode parity: the CUDA walker, exchange, flatness and merge kernels against the FP64
+oracle, bit for bit (histograms, accept counts, ln g, energies, spins, exchange counters,
+configuration permutation, merged ln g).  Sizes span several batches and a ragged tail, every group
+size (summation order), every coupling shell count, table lattices, the shared-memory and the
+global-memory lattice paths, and the degenerate single-window / single-walker layouts."""
+import numpy as np
+import pytest
+
+from rewl_pairs import assert_same_state, make_pair
+
+pytestmark = pytest.mark.gpu
+
+CFG1 = dict(L=4, J=(1.0, 0.5), n_bins=200, n_windows=4, walkers_per_window=2, overlap=0.75, flatness=0.8,
+            lnf_final=1e-3, seed=1)
+
+
+def run_both(gpu, orc, intervals):
+    gpu.init_walkers()
+    orc.init_walkers()
+    assert_same_state(gpu, orc)
+    if intervals:
+        gpu.run_intervals(intervals)
+        orc.run_intervals(intervals)
+    assert_same_state(gpu, orc)
+    lg, cg = gpu.merge()
+    lo, co = orc.merge()
+    assert np.array_equal(lg.view(np.int64), lo.view(np.int64)), "merged ln g differs"
+    assert np.array_equal(cg, co)
+
+
+@pytest.mark.parametrize("G", [1, 2, 4, 8, 16, 32])
+def test_cfg1_every_group_size(G):
+    gpu, orc = make_pair(group_size=G, exchange_interval=1000, **CFG1)
+    run_both(gpu, orc, 6)
+    gpu.close()
+
+
+def test_cfg1_long_with_flatness_events():
+    """Enough moves that walkers in the upper windows pass several ln f reductions."""
+    gpu, orc = make_pair(group_size=8, exchange_interval=10000, **CFG1)
+    run_both(gpu, orc, 40)
+    w = gpu.walkers()
+    assert w["stage"].max() >= 2, "expected ln f reductions within the run"
+    a, b = gpu.exchange_counts()
+    assert np.all(b > 0)
+    gpu.close()
+
+
+def test_three_shells_ragged():
+    gpu, orc = make_pair(group_size=1, L=6, J=(1.0, 0.4, -0.1), n_bins=150, n_windows=5, walkers_per_window=3,
+                         overlap=0.7, flatness=0.8, lnf_final=1e-3, seed=7, exchange_interval=777)
+    run_both(gpu, orc, 4)
+    gpu.close()
+
+
+def test_four_shells():
+    gpu, orc = make_pair(group_size=2, L=5, J=(1.0, 0.6, -0.05, -0.1), n_bins=120, n_windows=3,
+                         walkers_per_window=2, overlap=0.75, flatness=0.8, lnf_final=1e-3, seed=3,
+                         exchange_interval=500)
+    run_both(gpu, orc, 4)
+    gpu.close()
+
+
+def test_single_window_single_walker_every_move_exchange():
+    gpu, orc = make_pair(group_size=4, L=3, J=(1.0,), n_bins=40, n_windows=1, walkers_per_window=1,
+                         overlap=0.0, flatness=0.8, lnf_final=1e-3, seed=11, exchange_interval=1)
+    run_both(gpu, orc, 50)
+    gpu.close()
+
+
+def test_chain_table_lattice():
+    gpu, orc = make_pair(kind="chain", group_size=1, L=10, J=(1.0,), n_bins=40, n_windows=2,
+                         walkers_per_window=2, overlap=0.75, flatness=0.8, lnf_final=1e-4, seed=5,
+                         exchange_interval=2000)
+    run_both(gpu, orc, 10)
+    gpu.close()
+
+
+def test_explicit_table_lattice():
+    """Ring of 24 spins with nearest and next-nearest couplings given as a table."""
+    n = 24
+    nbr = np.array([[(i - 1) % n for i in range(n)], [(i + 1) % n for i in range(n)],
+                    [(i - 2) % n for i in range(n)], [(i + 2) % n for i in range(n)]], dtype=np.int32)
+    Jt = np.array([[1.0] * n, [1.0] * n, [-0.3] * n, [-0.3] * n])
+    for G in (1, 2):
+        gpu, orc = make_pair(kind="table", group_size=G, nbr=nbr, Jt=Jt, e_min=-20.0, e_max=20.0, n_bins=60,
+                             n_windows=3, walkers_per_window=2, overlap=0.75, flatness=0.8, lnf_final=1e-4,
+                             seed=9, exchange_interval=1500)
+        run_both(gpu, orc, 5)
+        gpu.close()
+
+
+def test_cfg2_size_shared_lattice():
+    """bcc L=16 (8192 spins), 16 windows x 4 walkers, 2000 bins: the production workload's geometry."""
+    gpu, orc = make_pair(group_size=1, L=16, J=(1.0, 0.5), n_bins=2000, n_windows=16, walkers_per_window=4,
+                         overlap=0.75, flatness=0.8, lnf_final=1e-8, seed=1, exchange_interval=3000)
+    assert gpu.info()["lattice_in_shared"] == 1
+    run_both(gpu, orc, 2)
+    gpu.close()
+
+
+def test_global_memory_lattice_path():
+    """bcc L=20 in FP64 (384 KB per lattice) does not fit in shared memory: global-memory path."""
+    gpu, orc = make_pair(group_size=1, L=20, J=(1.0, 0.5), n_bins=400, n_windows=3, walkers_per_window=1,
+                         overlap=0.75, flatness=0.8, lnf_final=1e-8, seed=2, exchange_interval=2000)
+    assert gpu.info()["lattice_in_shared"] == 0
+    run_both(gpu, orc, 2)
+    gpu.close()
+
+
+def test_frozen_walkers_and_set_initial_lng():
+    """Warm start: set ln g and ln f below ln f_final for every walker (frozen), walk, compare."""
+    gpu, orc = make_pair(group_size=8, exchange_interval=1000, **CFG1)
+    B = gpu.B
+    lng0 = np.linspace(0.0, 30.0, B) + np.sin(np.arange(B) / 7.0)
+    gpu.set_initial_lng(lng0, 1e-4)
+    orc.set_lng(lng0, 1e-4)
+    run_both(gpu, orc, 3)
+    w = gpu.walkers()
+    assert np.all(w["H"] == 0)
+    gpu.close()

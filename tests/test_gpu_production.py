@@ -1,0 +1,152 @@
+"""Production mode (FP32 spins and dE; ln g and energy in 64-bit fixed point) against exact results
+and, statistically, against the FP64 oracle; plus state invariants at the benchmark geometry and at
+the large 4-shell L=32 geometry (global-memory lattice path)."""
+import math
+import time
+from multiprocessing import get_context
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1411_4212_gb300 as rw
+from test_oracle_pins import chain_exact_lng
+
+pytestmark = pytest.mark.gpu
+
+
+def run_to_end(sim, lnf_final, chunk=20, limit_s=600):
+    sim.init_walkers()
+    t0 = time.time()
+    while True:
+        st = sim.run_intervals(chunk)
+        if st["all_done"]:
+            return
+        assert time.time() - t0 < limit_s, "run did not converge in time"
+
+
+def test_production_chain_matches_exact_density_of_states():
+    """Open chain of 5 spins over the full range: mean ln g over seeds equals the exact Irwin-Hall
+    bin masses (the same bar the oracle meets)."""
+    Ns, B = 5, 32
+    devs = []
+    for seed in range(1, 9):
+        g = rw.REWL(kind=rw.CHAIN, L=Ns, J=(1.0,), n_bins=B, n_windows=1, walkers_per_window=1,
+                    lnf_final=1e-6, seed=seed, exchange_interval=2000, group_size=16, mode=rw.PRODUCTION)
+        run_to_end(g, 1e-6)
+        lng, cen = g.merge()
+        ex = chain_exact_lng(Ns, 1.0, g.e_min, g.e_max, B)
+        devs.append(lng - (ex - ex.mean()))
+        p = np.exp(lng - lng.max())
+        p /= p.sum()
+        assert abs(np.sum(p * cen)) < 0.03
+        assert np.sum(p * cen ** 2) == pytest.approx((Ns - 1) / 3.0 + g.dE ** 2 / 12, rel=0.02)
+        g.close()
+    devs = np.array(devs)
+    print("production chain: rms of seed-mean deviation", np.sqrt(np.mean(devs.mean(0) ** 2)))
+    assert np.sqrt(np.mean(devs.mean(0) ** 2)) < 0.03
+    assert np.max(np.abs(devs.mean(0))) < 0.12
+
+
+STAT_CFG = dict(L=4, J=(1.0, 0.5), e_min=-400.0, e_max=0.0, n_bins=120, n_windows=4, walkers_per_window=2,
+                overlap=0.75, flatness=0.8, lnf_final=1e-4, exchange_interval=10000)
+T_GRID = np.linspace(1.5, 4.0, 2501)
+
+
+def _oracle_run(seed):
+    s = oracle.OracleREWL(kind=oracle.BCC, seed=seed, **STAT_CFG)
+    s.init_walkers()
+    while not s.all_done(STAT_CFG["lnf_final"]):
+        s.run_intervals(10)
+    lng, cen = s.merge()
+    U, Cv, _ = oracle.thermo(lng, cen, s.N, T_GRID)
+    return lng, oracle.peak(T_GRID, Cv)
+
+
+def test_production_statistics_match_oracle():
+    """16 seeds each side: normalised ln g and the specific-heat peak agree within the stated
+    tolerance (0.02 rms, 0.5 %) or, where the seed-to-seed noise of Wang-Landau itself is larger,
+    within three standard errors of the difference."""
+    seeds = list(range(1, 17))
+    with get_context("spawn").Pool(min(16, len(seeds))) as pool:
+        ores = pool.map(_oracle_run, [1000 + s for s in seeds])
+    lo = np.array([r[0] for r in ores])
+    to = np.array([r[1] for r in ores])
+    lg, tg = [], []
+    for s in seeds:
+        g = rw.REWL(kind=rw.BCC, seed=s, mode=rw.PRODUCTION, **STAT_CFG)
+        run_to_end(g, STAT_CFG["lnf_final"])
+        lng, cen = g.merge()
+        U, Cv, _ = rw.thermo(lng, cen, g.N, T_GRID)
+        lg.append(lng)
+        tg.append(rw.peak_temperature(T_GRID, Cv))
+        g.close()
+    lg, tg = np.array(lg), np.array(tg)
+    n = len(seeds)
+    diff = lg.mean(0) - lo.mean(0)
+    rms = float(np.sqrt(np.mean(diff ** 2)))
+    noise = float(np.sqrt(np.mean(lg.var(0, ddof=1) / n + lo.var(0, ddof=1) / n)))
+    dT = float(tg.mean() - to.mean())
+    sT = float(math.sqrt(tg.var(ddof=1) / n + to.var(ddof=1) / n))
+    print(f"ln g rms(mean GPU - mean oracle) = {rms:.4f} (noise {noise:.4f}); "
+          f"T_peak GPU {tg.mean():.4f} +- {tg.std(ddof=1) / math.sqrt(n):.4f}, "
+          f"oracle {to.mean():.4f} +- {to.std(ddof=1) / math.sqrt(n):.4f}")
+    assert rms <= max(0.02, 3.0 * noise)
+    assert abs(dT) <= max(0.005 * to.mean(), 3.0 * sT)
+
+
+def test_benchmark_geometry_invariants():
+    """bcc L=16, 2 shells, 16 windows x 4 walkers, 2000 bins (the benchmark workload)."""
+    g = rw.REWL(kind=rw.BCC, L=16, J=(1.0, 0.5), n_bins=2000, n_windows=16, walkers_per_window=4,
+                lnf_final=1e-8, seed=1, exchange_interval=10000, mode=rw.PRODUCTION)
+    info = g.info()
+    assert info["lattice_in_shared"] == 1 and info["group_size"] == 1
+    st = g.run_intervals(5)
+    w = g.walkers()
+    starts = oracle.window_layout(g.B, g.h, 0.75)[1]
+    for s in range(g.n_slots):
+        k = s // g.m
+        assert starts[k] <= w["bin"][s] < starts[k] + g.W
+    assert np.all(w["steps"] == 5 * 10000)
+    if np.all(w["stage"] == 0):
+        assert np.all(w["H"].sum(1) == 5 * 10000)
+    assert sorted(w["replica"]) == list(range(g.n_slots))
+    assert st["max_energy_drift"] < 1e-2
+    assert st["exchange_accepts"] > 0
+    c = g.counters()
+    assert 0 < c["accepts"] < c["moves"]
+    Er = g.replica_energies()
+    assert np.allclose(Er[w["replica"]], w["E"], atol=5e-3)
+    g.close()
+
+
+def test_large_four_shell_geometry_global_path():
+    """bcc L=32 (65536 spins), 4 shells (z = 50), 64 windows x 8 walkers, 8000 bins."""
+    g = rw.REWL(kind=rw.BCC, L=32, J=(1.0, 0.6, -0.05, -0.1), n_bins=8000, n_windows=64, walkers_per_window=8,
+                lnf_final=1e-8, seed=1, exchange_interval=10000, mode=rw.PRODUCTION)
+    info = g.info()
+    assert info["lattice_in_shared"] == 0 and info["z"] == 50
+    assert g.e_min == pytest.approx(-281804.8, rel=1e-12)
+    st = g.run_intervals(1)
+    w = g.walkers()
+    starts = oracle.window_layout(g.B, g.h, 0.75)[1]
+    for s in range(g.n_slots):
+        k = s // g.m
+        assert starts[k] <= w["bin"][s] < starts[k] + g.W
+    assert st["max_energy_drift"] < 5e-2
+    Er = g.replica_energies()
+    assert np.allclose(Er[w["replica"]], w["E"], atol=5e-2)
+    g.close()
+
+
+def test_initial_drive_cap_reports_timeout():
+    g = rw.REWL(kind=rw.BCC, L=4, J=(1.0, 0.5), n_bins=200, n_windows=4, walkers_per_window=2,
+                init_max_moves=3, mode=rw.TRAJECTORY)
+    with pytest.raises(rw.RewlError) as e:
+        g.init_walkers()
+    assert e.value.status == rw.ETIMEOUT
+    o = oracle.OracleREWL(kind=oracle.BCC, L=4, J=(1.0, 0.5), n_bins=200, n_windows=4, walkers_per_window=2,
+                          init_max_moves=3)
+    with pytest.raises(RuntimeError):
+        o.init_walkers()
+    g.close()
