@@ -90,8 +90,9 @@ typedef struct {
   int64_t exchange_interval;     /* trial moves per walker between replica exchanges (> 0) */
   int64_t max_moves_per_stage;   /* cap for rewl_run_stage (moves per walker); 0 = no cap */
   int64_t init_max_moves;        /* cap for the initial drive into the windows; 0 = 2^40 */
-  int32_t recompute_every;       /* production: full FP64 energy recomputation every this many
-                                    intervals (0 = every interval) */
+  int32_t recompute_every;       /* full energy recomputation every this many intervals; 0 =
+                                    default (production 8: replaces the running energy;
+                                    trajectory 1: drift diagnostic only) */
   int32_t reserved;
   double lnf_initial;            /* initial ln f; 0 = 1 (f0 = e, Sec. 4.2) */
   double timeout_s;              /* wall-clock cap for rewl_run_stage (0 = none) */
@@ -122,7 +123,7 @@ typedef struct {
   int64_t intervals_done;
   size_t shared_bytes_per_walker;
   int32_t lattice_in_shared;   /* 1 when each walker's spins live in shared memory */
-  int32_t reserved;
+  int32_t pipelined;           /* 1 when the Wang-Landau moves run on the warp-specialised walker */
 } rewl_info;
 
 typedef struct {

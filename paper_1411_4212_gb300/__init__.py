@@ -73,7 +73,7 @@ class Info(C.Structure):
                 ("e_min", C.c_double), ("e_max", C.c_double), ("bin_width", C.c_double),
                 ("initial_energy", C.c_double), ("exchange_index", C.c_int64), ("intervals_done", C.c_int64),
                 ("shared_bytes_per_walker", C.c_size_t), ("lattice_in_shared", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("pipelined", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -166,7 +166,7 @@ class REWL:
     def __init__(self, kind=BCC, L=4, J=(1.0, 0.5), nbr=None, Jt=None, e_min=math.nan, e_max=math.nan,
                  n_bins=200, n_windows=4, walkers_per_window=2, overlap=0.75, flatness=0.8,
                  lnf_final=1e-3, seed=1, mode=PRODUCTION, group_size=0, exchange_interval=10000,
-                 max_moves_per_stage=0, init_max_moves=0, recompute_every=1, lnf_initial=0.0,
+                 max_moves_per_stage=0, init_max_moves=0, recompute_every=0, lnf_initial=0.0,
                  timeout_s=0.0, stream=None):
         lib = load_library()
         lat = Lattice()

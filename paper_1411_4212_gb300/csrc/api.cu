@@ -36,6 +36,10 @@ struct rewl_handle {
   ExpCoeffs ex{};
   bool smem_lattice = false;
   size_t smem_bytes = 0;
+  bool pipe = false;              // warp-specialised walker for the Wang-Landau moves
+  bool pipe_smem_lattice = false;
+  size_t pipe_smem_bytes = 0;
+  int own_entries = 0;
 
   void* d_spins = nullptr;
   int32_t* d_perm = nullptr;
@@ -195,6 +199,10 @@ Windows windows_of(rewl_handle* h) {
   w.e_min = h->e_min;
   w.dE = h->dE;
   w.dq_scale = (float)(kEnergyScale / h->dE);
+  w.dq_scale64 = kEnergyScale / h->dE;
+  const double s24 = 16777216.0 / h->dE;
+  w.dq24_hi = (float)s24;
+  w.dq24_lo = (float)(s24 - (double)w.dq24_hi);
   return w;
 }
 
@@ -211,7 +219,14 @@ WalkerArgs walker_args(rewl_handle* h, bool init, bool recompute, long long move
   a.init = init ? 1 : 0;
   a.recompute = recompute ? 1 : 0;
   a.lnf_final = h->lnf_final;
+  a.own_mask = h->own_entries > 0 ? h->own_entries - 1 : 0;
   return a;
+}
+
+// The Wang-Landau moves of one exchange interval (the initial drive always uses the batch walker).
+cudaError_t launch_walk(rewl_handle* h, const WalkerArgs& a) {
+  if (h->pipe) return launch_walkers_pipe(a, h->S, h->traj, h->pipe_smem_lattice, h->pipe_smem_bytes, h->stream);
+  return launch_walkers(a, h->S, h->traj, h->smem_lattice, h->smem_bytes, h->stream);
 }
 
 ExpCoeffs exp_coeffs() {
@@ -273,7 +288,7 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   h->exchange_interval = cfg->exchange_interval;
   h->max_moves_per_stage = cfg->max_moves_per_stage;
   h->init_cap = cfg->init_max_moves > 0 ? cfg->init_max_moves : (1LL << 40);
-  h->recompute_every = cfg->recompute_every > 0 ? cfg->recompute_every : 1;
+  h->recompute_every = cfg->recompute_every > 0 ? cfg->recompute_every : (h->traj ? 1 : 8);
   h->timeout_s = cfg->timeout_s;
   h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
   h->ex = exp_coeffs();
@@ -301,8 +316,14 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
     g.L = h->L;
     g.divL = (uint32_t)((0x100000000ULL + (unsigned long long)h->L - 1) / (unsigned long long)h->L);
     g.r2max = 0;
+    g.n_shells = cpl->n_shells;
+    for (int s2 = 0; s2 < 4; ++s2) {
+      g.Jsh_d[s2] = s2 < cpl->n_shells ? cpl->J[s2] : 0.0;
+      g.Jsh_f[s2] = (float)g.Jsh_d[s2];
+    }
     for (int j = 0; j < z; ++j) {
-      g.off[j] = (uint32_t)(off[j][0] + 8) | ((uint32_t)(off[j][1] + 8) << 8) | ((uint32_t)(off[j][2] + 8) << 16);
+      g.off[j] = (uint32_t)(off[j][0] + 8) | ((uint32_t)(off[j][1] + 8) << 8) | ((uint32_t)(off[j][2] + 8) << 16) |
+                 ((uint32_t)shell[j] << 24);
       g.Jd[j] = cpl->J[shell[j]];
       g.Jf[j] = (float)cpl->J[shell[j]];
       g.r2max = std::max(g.r2max, off[j][0] * off[j][0] + off[j][1] * off[j][1] + off[j][2] * off[j][2]);
@@ -318,11 +339,12 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
       j0 = j1;
     }
     g.energy_weight = 1.0f;
-    // E0 = -1/2 sum_i sum_j J_ij for the aligned state, site by site in slot order
+    // E0 = -1/2 sum_i sum_j J_ij for the aligned state, site by site in slot order (production
+    // uses the FP32 couplings its energy changes are computed with)
     double acc = 0.0;
     for (int i = 0; i < h->N; ++i) {
       double row = 0.0;
-      for (int j = 0; j < z; ++j) row = row + Jslot[j];
+      for (int j = 0; j < z; ++j) row = row + (h->traj ? Jslot[j] : (double)(float)Jslot[j]);
       acc = acc + row;
     }
     h->E0 = -0.5 * acc;
@@ -372,7 +394,10 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
     double acc = 0.0;
     for (int i = 0; i < N; ++i) {
       double row = 0.0;
-      for (int j = 0; j < z; ++j) row = row + h->tab_J[(size_t)j * N + i];
+      for (int j = 0; j < z; ++j) {
+        const double Jij = h->tab_J[(size_t)j * N + i];
+        row = row + (h->traj ? Jij : (double)(float)Jij);
+      }
       acc = acc + row;
     }
     h->E0 = -0.5 * acc;
@@ -405,10 +430,17 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
 
   // ---- lanes per move ----
   if (cfg->group_size == 0) {
-    const double kk = std::sqrt(2.0 * h->N / (h->z + 1.0));
-    int K = 1;
-    while (K * 2 <= kk && K < 32) K *= 2;
-    h->G = 32 / K;
+    // one lane per move (the warp-specialised walker, 64-move speculation window) when few moves
+    // are expected to need re-evaluation: 63 (z+1) / N * (acceptance ~ 1/2) < 1/4; else the batch
+    // walker with K = 32/G moves per batch, K ~ sqrt(2 N / (z+1))
+    if (lat->kind == REWL_LATTICE_BCC && 63.0 * (h->z + 1.0) / h->N * 0.5 < 0.25) {
+      h->G = 1;
+    } else {
+      const double kk = std::sqrt(2.0 * h->N / (h->z + 1.0));
+      int K = 1;
+      while (K * 2 <= kk && K < 32) K *= 2;
+      h->G = 32 / K;
+    }
   } else {
     const int G = cfg->group_size;
     if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32) return bad("group_size must be 0, 1, 2, 4, 8, 16 or 32");
@@ -428,6 +460,27 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   h->smem_lattice = with_lattice + 1024 <= (size_t)max_smem;
   h->smem_bytes = walker_smem_bytes(h->traj, h->smem_lattice, h->N, h->W);
   if (h->smem_bytes + 1024 > (size_t)max_smem) return bad("window tables do not fit in shared memory");
+  // warp-specialised walker: bcc, one lane per move; owner table as large as the lattice (<= 8192
+  // entries), shrunk when the lattice itself occupies shared memory
+  // (energy increments travel as int32 in 2^-24 bins: |dE| <= 2 sum_j |J_j| must stay below 100 bins)
+  double max_dE = 0.0;
+  for (int j = 0; j < h->z && g.kind == 0; ++j) max_dE += 2.0 * std::fabs(g.Jd[j]);
+  if (g.kind == 0 && h->G == 1 && max_dE < 100.0 * h->dE) {
+    int own_full = 256;
+    while (own_full < h->N && own_full < 8192) own_full *= 2;
+    const size_t base = walker_pipe_smem_bytes(h->traj, true, h->N, h->W, 0);
+    if (base + 1024 + 256 * 8 <= (size_t)max_smem) {
+      int e = own_full;
+      while (e > 256 && base + 1024 + 8 * (size_t)e > (size_t)max_smem) e /= 2;
+      h->own_entries = e;
+      h->pipe_smem_lattice = true;
+    } else {
+      h->own_entries = own_full;
+      h->pipe_smem_lattice = false;
+    }
+    h->pipe_smem_bytes = walker_pipe_smem_bytes(h->traj, h->pipe_smem_lattice, h->N, h->W, h->own_entries);
+    h->pipe = h->pipe_smem_bytes + 1024 <= (size_t)max_smem;
+  }
 
   const size_t S = h->S, W = h->W, N = h->N;
   const size_t real = h->traj ? sizeof(double) : sizeof(float);
@@ -587,7 +640,7 @@ rewl_status rewl_walk(rewl_handle* h) {
   }
   const bool recompute = ((h->intervals_done + 1) % h->recompute_every) == 0;
   const WalkerArgs a = walker_args(h, false, recompute, h->exchange_interval);
-  CUDA_TRY(h, launch_walkers(a, h->S, h->traj, h->smem_lattice, h->smem_bytes, h->stream));
+  CUDA_TRY(h, launch_walk(h, a));
   h->intervals_done += 1;
   return REWL_OK;
 }
@@ -615,7 +668,7 @@ static rewl_status enqueue_intervals(rewl_handle* h, int n) {
   for (int i = 0; i < n; ++i) {
     const bool recompute = ((h->intervals_done + 1) % h->recompute_every) == 0;
     const WalkerArgs a = walker_args(h, false, recompute, h->exchange_interval);
-    CUDA_TRY(h, launch_walkers(a, h->S, h->traj, h->smem_lattice, h->smem_bytes, h->stream));
+    CUDA_TRY(h, launch_walk(h, a));
     CUDA_TRY(h, launch_exchange(ea, h->stream));
     CUDA_TRY(h, launch_flatness(fa, h->S, h->stream));
     h->intervals_done += 1;
@@ -925,8 +978,9 @@ rewl_status rewl_get_info(const rewl_handle* hc, rewl_info* out) {
   if (!h->broken && cudaMemcpy(&ex, h->d_ex_index, sizeof ex, cudaMemcpyDeviceToHost) != cudaSuccess) ex = -1;
   out->exchange_index = ex;
   out->intervals_done = h->intervals_done;
-  out->shared_bytes_per_walker = h->smem_bytes;
-  out->lattice_in_shared = h->smem_lattice ? 1 : 0;
+  out->shared_bytes_per_walker = h->pipe ? h->pipe_smem_bytes : h->smem_bytes;
+  out->lattice_in_shared = (h->pipe ? h->pipe_smem_lattice : h->smem_lattice) ? 1 : 0;
+  out->pipelined = h->pipe ? 1 : 0;
   return REWL_OK;
 }
 

@@ -80,7 +80,8 @@ __device__ __forceinline__ int bcc_offset_site(int X, int Y, int Z, int dx, int 
   return ((((z >> 1) * L + (y >> 1)) * L + (x >> 1)) << 1) + (x & 1);
 }
 
-// Offsets are packed as three biased bytes: (dx + 8) | (dy + 8) << 8 | (dz + 8) << 16.
+// Offsets are packed as three biased bytes and the shell: (dx + 8) | (dy + 8) << 8 | (dz + 8) << 16 |
+// shell << 24.
 __device__ __forceinline__ void unpack_offset(uint32_t p, int& dx, int& dy, int& dz) {
   dx = (int)(p & 0xffu) - 8;
   dy = (int)((p >> 8) & 0xffu) - 8;

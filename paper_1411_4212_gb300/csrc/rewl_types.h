@@ -17,9 +17,12 @@ struct Geometry {
   int N, z, L;
   uint32_t divL;                       // ceil(2^32 / L) for bcc
   int r2max;                           // bcc: largest squared half-unit offset of the shells
-  uint32_t off[kMaxSlotsPerSite];      // bcc: packed offsets (see unpack_offset)
+  uint32_t off[kMaxSlotsPerSite];      // bcc: packed offsets and shell (see unpack_offset)
   float Jf[kMaxSlotsPerSite];          // bcc: coupling per slot
   double Jd[kMaxSlotsPerSite];
+  int n_shells;                        // bcc: 1..4
+  float Jsh_f[4];                      // bcc: coupling per shell
+  double Jsh_d[4];
   int n_energy_slots;                  // slots summed by the energy recomputation
   float energy_weight;                 // 1 (bcc, forward half of every shell) or 0.5 (table, all)
   uint8_t energy_slot[kMaxSlotsPerSite];
@@ -32,7 +35,9 @@ struct Windows {
   int B, h, m, W;
   const int32_t* starts;               // [h]
   double e_min, dE;                    // bin b covers [e_min + b dE, e_min + (b+1) dE)
-  float dq_scale;                      // 2^32 / dE (production energy increments)
+  float dq_scale;                      // 2^32 / dE (FP32 copy, unused by the walk)
+  double dq_scale64;                   // 2^32 / dE: production energy increment dq = rint(dE * scale)
+  float dq24_hi, dq24_lo;              // 2^24 / dE split into two floats (hi + lo, ~48 bits)
 };
 
 struct WalkerState {
@@ -69,6 +74,7 @@ struct WalkerArgs {
   int G;                               // lanes per trial move
   int init;                            // 1: initial drive into the windows
   int recompute;                       // 1: energy recomputation at the end of the launch
+  int own_mask;                        // pipelined walker: owner-table size - 1 (power of two)
   double lnf_final;
 };
 

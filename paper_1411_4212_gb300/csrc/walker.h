@@ -11,6 +11,11 @@ size_t walker_smem_bytes(bool traj, bool smem_lattice, int N, int W);
 cudaError_t launch_walkers(const WalkerArgs& a, int n_slots, bool traj, bool smem_lattice, size_t smem,
                            cudaStream_t stream);
 
+// Warp-specialised walker (bcc lattices, one lane per trial move, Wang-Landau moves only).
+size_t walker_pipe_smem_bytes(bool traj, bool smem_lattice, int N, int W, int own_entries);
+cudaError_t launch_walkers_pipe(const WalkerArgs& a, int n_slots, bool traj, bool smem_lattice, size_t smem,
+                                cudaStream_t stream);
+
 struct ExchangeArgs {
   Windows win;
   WalkerState st;

@@ -1,0 +1,687 @@
+// walker_pipe.cu -- warp-specialised Wang-Landau walker for bcc lattices, one lane per trial move
+// (Sec. 4.2, Eq. 4; trial move Sec. 4.4).
+//
+// One CTA per walker slot.  Warp 1 (producer) prepares batch b+1 of 32 trial moves while warp 0
+// (resolver) resolves batch b strictly in order, so the walk is the sequential Markov chain:
+//   producer: Philox draws, the local field h_i = sum_j J_ij S_j over the coupling shells (bcc
+//     offsets known at compile time, all neighbour loads issued at once), dE = -(S'-S).h, and two
+//     conflict masks read from a shared-memory owner table -- the moves of batch b (still being
+//     resolved while batch b+1 reads the lattice) and the earlier moves of batch b+1 that sit on the
+//     same site or a neighbouring one;
+//   resolver: a move whose mask meets a move accepted since the lattice was read is re-evaluated on
+//     the current lattice; then accept with min[1, g(E)/g(E')] (reject outside the window) and add
+//     ln f to ln g and 1 to H at the resulting state.
+// The owner table may alias sites (hashed) -- an alias only causes an exact re-evaluation.  Two
+// record buffers alternate; named barriers READY(b mod 2) and DONE(b mod 2) order the hand-over, so
+// the producer reads the lattice only after every move of batch b-1 has been written.
+#include <cstring>
+
+#include "walker_common.cuh"
+
+namespace rewl {
+
+struct ShellTable {
+  int dx[kMaxSlotsPerSite], dy[kMaxSlotsPerSite], dz[kMaxSlotsPerSite], sh[kMaxSlotsPerSite];
+  int z;
+};
+
+// Canonical bcc slot order: shell by shell (squared half-unit lengths 3, 4, 8, 11), lexicographic
+// (dx, dy, dz) inside a shell.
+constexpr ShellTable make_shells(int nsh) {
+  ShellTable t{};
+  constexpr int r2s[4] = {3, 4, 8, 11};
+  int z = 0;
+  for (int s = 0; s < nsh; ++s)
+    for (int a = -3; a <= 3; ++a)
+      for (int b = -3; b <= 3; ++b)
+        for (int c = -3; c <= 3; ++c) {
+          if (((a ^ b) & 1) != 0 || ((b ^ c) & 1) != 0) continue;
+          if (a * a + b * b + c * c != r2s[s]) continue;
+          t.dx[z] = a;
+          t.dy[z] = b;
+          t.dz[z] = c;
+          t.sh[z] = s;
+          ++z;
+        }
+  t.z = z;
+  return t;
+}
+
+constexpr int kPairThreads = 64;   // resolver warp + producer warp
+
+__host__ __device__ constexpr size_t align16(size_t n) { return (n + 15) & ~(size_t)15; }
+constexpr int kBarReady = 1;       // ids 1, 2
+constexpr int kBarDone = 3;        // ids 3, 4
+
+__device__ __forceinline__ void named_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kPairThreads) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kPairThreads) : "memory");
+}
+
+template <bool kTraj>
+struct alignas(16) Rec;
+template <>
+struct alignas(16) Rec<false> {
+  long long dq;          // energy increment, 2^-32 bins (a 2^-24-bin integer shifted left by 8)
+  int lu;                // ln u, 2^-20 units
+  uint32_t cprev;        // batch b-1 moves touching this move's neighbourhood
+  uint32_t ccur;         // earlier moves of this batch touching it
+  int site;
+  float nx, ny;
+  float nz;
+  int pad[3];
+};
+template <>
+struct alignas(16) Rec<true> {
+  double dE;
+  double u;
+  uint32_t cprev, ccur;
+  int site, pad;
+  double nx, ny, nz, pad2;
+};
+
+// Local field of (X, Y, Z) by one lane over all slots in canonical order, with the owner-table
+// words of the site's neighbours OR-ed into own0 / own1.
+template <bool kTraj, int NSH>
+__device__ __forceinline__ void field_one_lane(const typename Mode<kTraj>::Real* __restrict__ sx,
+                                               const typename Mode<kTraj>::Real* __restrict__ sy,
+                                               const typename Mode<kTraj>::Real* __restrict__ sz, int X, int Y, int Z,
+                                               int L, const typename Mode<kTraj>::Real (&Jsh)[4],
+                                               typename Mode<kTraj>::Real& hx, typename Mode<kTraj>::Real& hy,
+                                               typename Mode<kTraj>::Real& hz, const uint2* own, uint32_t omask,
+                                               uint32_t& own0, uint32_t& own1) {
+  using Real = typename Mode<kTraj>::Real;
+  constexpr ShellTable T = make_shells(NSH);
+  const int twoL = 2 * L, LL = L * L;
+  int xw[7], yw[7], zw[7];
+#pragma unroll
+  for (int d = -3; d <= 3; ++d) {
+    int x = X + d, y = Y + d, z = Z + d;
+    x += (x < 0) ? twoL : 0;
+    x -= (x >= twoL) ? twoL : 0;
+    y += (y < 0) ? twoL : 0;
+    y -= (y >= twoL) ? twoL : 0;
+    z += (z < 0) ? twoL : 0;
+    z -= (z >= twoL) ? twoL : 0;
+    xw[d + 3] = x;
+    yw[d + 3] = L * y;
+    zw[d + 3] = LL * z;
+  }
+  // site = x' + L y' + L^2 z' - s' (L + L^2), s' the neighbour's sublattice
+  const int s = X & 1;
+  const int par_same = s * (L + LL), par_flip = (s ^ 1) * (L + LL);
+  hx = Real(0);
+  hy = Real(0);
+  hz = Real(0);
+  // production: per-shell spin sums first, then one coupling per shell -- fewer roundings, and
+  // none at all for aligned spins (whose dE would otherwise carry the same rounding every move)
+  Real tx[4] = {Real(0), Real(0), Real(0), Real(0)}, ty[4] = {Real(0), Real(0), Real(0), Real(0)},
+       tz[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+  for (int j = 0; j < T.z; ++j) {
+    const int n = xw[T.dx[j] + 3] + yw[T.dy[j] + 3] + zw[T.dz[j] + 3] - ((T.dx[j] & 1) ? par_flip : par_same);
+    if constexpr (kTraj) {
+      const Real J = Jsh[T.sh[j]];
+      hx = __dadd_rn(hx, __dmul_rn(J, sx[n]));
+      hy = __dadd_rn(hy, __dmul_rn(J, sy[n]));
+      hz = __dadd_rn(hz, __dmul_rn(J, sz[n]));
+    } else {
+      tx[T.sh[j]] += sx[n];
+      ty[T.sh[j]] += sy[n];
+      tz[T.sh[j]] += sz[n];
+    }
+    const uint2 o = own[n & omask];
+    own0 |= o.x;
+    own1 |= o.y;
+  }
+  if constexpr (!kTraj) {
+#pragma unroll
+    for (int s2 = 0; s2 < NSH; ++s2) {
+      hx = fmaf(Jsh[s2], tx[s2], hx);
+      hy = fmaf(Jsh[s2], ty[s2], hy);
+      hz = fmaf(Jsh[s2], tz[s2], hz);
+    }
+  }
+}
+
+// Uniform in [1, 2) from the top 23 bits of a word (no integer-to-float conversion).
+__device__ __forceinline__ float one_to_two(uint32_t x) { return __uint_as_float(0x3f800000u | (x >> 9)); }
+
+// dE (FP32) -> int32 in 2^-24 bins: dE * (hi + lo) with the product of the head exact (fmaf).
+__device__ __forceinline__ int dq24_of(float dE, const Windows& w) {
+  const float p = dE * w.dq24_hi;
+  const float e = fmaf(dE, w.dq24_hi, -p) + dE * w.dq24_lo;
+  return __float2int_rn(p) + __float2int_rn(e);
+}
+
+template <bool kTraj, bool kSmem, int NSH>
+__global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const WalkerArgs a) {
+  using Real = typename Mode<kTraj>::Real;
+  using Lng = typename Mode<kTraj>::Lng;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[kWalkerThreads / 32];
+
+  const int slot = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int N = a.geo.N, W = a.win.W, L = a.geo.L;
+  const int wlo = a.win.starts[slot / a.win.m];
+  const int rep = a.st.perm[slot];
+  const uint32_t omask = (uint32_t)a.own_mask;
+
+  // shared layout: ln g | H | offsets | J per slot | records[2][32] | owner table | spins
+  // (every section starts on a 16-byte boundary)
+  unsigned char* p = smem_raw;
+  Lng* lng_s = reinterpret_cast<Lng*>(p);
+  p += align16(sizeof(Lng) * (size_t)W);
+  uint32_t* H_s = reinterpret_cast<uint32_t*>(p);
+  p += align16((size_t)W * 4);
+  uint32_t* off_s = reinterpret_cast<uint32_t*>(p);
+  p += 4 * kMaxSlotsPerSite;
+  Real* J_s = reinterpret_cast<Real*>(p);
+  p += sizeof(Real) * kMaxSlotsPerSite;
+  Rec<kTraj>* rec = reinterpret_cast<Rec<kTraj>*>(p);
+  p += sizeof(Rec<kTraj>) * 64;
+  uint2* own = reinterpret_cast<uint2*>(p);
+  p += sizeof(uint2) * ((size_t)omask + 1);
+  Real* spin_s = reinterpret_cast<Real*>(p);
+
+  Real* gsp = reinterpret_cast<Real*>(a.st.spins) + (size_t)rep * 3 * N;
+  Real* sx = kSmem ? spin_s : gsp;
+  Real* sy = sx + N;
+  Real* sz = sx + 2 * (size_t)N;
+
+  const size_t lbase = (size_t)slot * W;
+  for (int w = tid; w < W; w += blockDim.x) {
+    if constexpr (kTraj)
+      lng_s[w] = (Lng)a.st.lng[lbase + w];
+    else
+      lng_s[w] = (Lng)a.st.lng_fx[lbase + w];
+    H_s[w] = a.st.H[lbase + w];
+  }
+  for (int j = tid; j < kMaxSlotsPerSite; j += blockDim.x) {
+    off_s[j] = a.geo.off[j];
+    J_s[j] = kTraj ? (Real)a.geo.Jd[j] : (Real)a.geo.Jf[j];
+  }
+  for (uint32_t i = tid; i <= omask; i += blockDim.x) own[i] = make_uint2(0u, 0u);
+  if (kSmem)
+    for (size_t i = tid; i < 3 * (size_t)N; i += blockDim.x) spin_s[i] = gsp[i];
+  __syncthreads();
+
+  const long long moves = a.moves;
+  const int nb = (int)((moves + 31) / 32);
+  const long long t0 = a.st.steps[slot];
+  const uint2 key = make_uint2((uint32_t)slot, a.key1);
+
+  if (warp == 1) {
+    // ------------------------------- producer -------------------------------
+    Real Jsh[4];
+#pragma unroll
+    for (int s2 = 0; s2 < 4; ++s2) Jsh[s2] = kTraj ? (Real)a.geo.Jsh_d[s2] : (Real)a.geo.Jsh_f[s2];
+    int site_prev = 0;
+    bool valid_prev = false;
+    for (int b = 0; b < nb; ++b) {
+      if (b >= 2) named_sync(kBarDone + (b & 1));
+      const int cur = b & 1;
+      const bool valid = (long long)b * 32 + lane < moves;
+      const unsigned long long t = (unsigned long long)(t0 + (long long)b * 32 + lane);
+      int site;
+      Real nx, ny, nz;
+      double u = 0.0;
+      int lu = 0;
+      if constexpr (kTraj) {
+        double dnx, dny, dnz;
+        draw_traj(key, t, false, N, site, u, dnx, dny, dnz);
+        nx = (Real)dnx;
+        ny = (Real)dny;
+        nz = (Real)dnz;
+      } else {
+        const uint4 x = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0u, 0u), key);
+        site = (int)__umulhi(x.x, (uint32_t)N);
+        const float uf = (one_to_two(x.y) - 1.0f) + 0x1.0p-24f;                // (0, 1)
+        lu = __float2int_rn(__logf(uf) * 1048576.0f);
+        const float zc = (2.0f * one_to_two(x.z) - 3.0f) + 0x1.0p-23f;          // (-1, 1), cos(theta)
+        float sn, cs;
+        __sincosf((one_to_two(x.w) - 1.5f) * 6.28318530717958648f, &sn, &cs);  // azimuth in [-pi, pi)
+        const float q = fmaxf(fmaf(-zc, zc, 1.0f), 0x1.0p-46f);
+        const float r = q * rsqrtf(q);                                          // sin(theta)
+        nx = (Real)(r * cs);
+        ny = (Real)(r * sn);
+        nz = (Real)zc;
+      }
+      int X, Y, Z;
+      bcc_coords(site, L, a.geo.divL, X, Y, Z);
+      uint32_t* own32 = reinterpret_cast<uint32_t*>(own);
+      if (valid) atomicOr(own32 + 2 * (site & omask) + cur, 1u << lane);
+      __syncwarp();
+      uint32_t o0 = 0, o1 = 0;
+      Real hx, hy, hz;
+      field_one_lane<kTraj, NSH>(sx, sy, sz, X, Y, Z, L, Jsh, hx, hy, hz, own, omask, o0, o1);
+      const uint2 oself = own[site & omask];
+      o0 |= oself.x;
+      o1 |= oself.y;
+      const uint32_t ocur = cur ? o1 : o0, oprev = cur ? o0 : o1;
+      const Real ox = sx[site], oy = sy[site], oz = sz[site];
+      Rec<kTraj>& r = rec[cur * 32 + lane];
+      if constexpr (kTraj) {
+        const double dx = __dsub_rn(nx, ox), dy = __dsub_rn(ny, oy), dz = __dsub_rn(nz, oz);
+        r.dE = -__dadd_rn(__dadd_rn(__dmul_rn(dx, hx), __dmul_rn(dy, hy)), __dmul_rn(dz, hz));
+        r.u = u;
+      } else {
+        const float dx = nx - ox, dy = ny - oy, dz = nz - oz;
+        const float dE = -fmaf(dz, hz, fmaf(dy, hy, dx * hx));
+        r.dq = (long long)dq24_of(dE, a.win) << 8;
+        r.lu = lu;
+      }
+      r.cprev = b > 0 ? oprev : 0u;
+      r.ccur = ocur & ((1u << lane) - 1u);
+      r.site = site;
+      r.nx = nx;
+      r.ny = ny;
+      r.nz = nz;
+      __syncwarp();
+      named_arrive(kBarReady + cur);
+      // batch b+1 inserts into the other slot, which still holds batch b-1's bits
+      if (valid_prev) own32[2 * (site_prev & omask) + (cur ^ 1)] = 0u;
+      __syncwarp();   // every clear lands before any lane inserts batch b+1
+      site_prev = site;
+      valid_prev = valid;
+    }
+    for (int b = nb - 2 > 0 ? nb - 2 : 0; b < nb; ++b) named_sync(kBarDone + (b & 1));
+  } else if (warp == 0) {
+   if constexpr (kTraj) {
+    // ------------------------ resolver (trajectory mode) ------------------------
+    double E = 0.0;
+    long long Efx = 0;
+    int bcur;
+    if constexpr (kTraj) {
+      E = a.st.E[slot];
+      bcur = a.st.bin[slot];
+    } else {
+      Efx = a.st.efx[slot];
+      bcur = fx_bin(Efx);
+    }
+    double lnf = 0.0;
+    long long lnf_fx = 0;
+    bool frozen;
+    if constexpr (kTraj) {
+      lnf = a.st.lnf[slot];
+      frozen = !(lnf >= a.lnf_final);
+    } else {
+      lnf_fx = a.st.lnf_fx[slot];
+      frozen = !((double)lnf_fx * kLngUnit >= a.lnf_final);
+    }
+    const bool bad = (unsigned)(bcur - wlo) >= (unsigned)W;
+    if (bad && lane == 0) atomicExch(a.st.ctrl + 0, kErrOutOfWindow);
+    Lng lng_cur = bad ? Lng(0) : lng_s[bcur - wlo];
+    uint32_t h_cur = bad ? 0u : H_s[bcur - wlo];
+    // ln g of the bins next to the current one, kept in registers (production)
+    long long lng_m = 0, lng_p = 0;
+    if constexpr (!kTraj) {
+      if (!bad) {
+        lng_m = bcur - 1 >= wlo ? (long long)lng_s[bcur - 1 - wlo] : 0;
+        lng_p = bcur + 1 < wlo + W ? (long long)lng_s[bcur + 1 - wlo] : 0;
+      }
+    }
+    constexpr int kWords = (int)(sizeof(Rec<kTraj>) / sizeof(int4));
+    uint32_t acc_prev = 0;
+    long long n_acc = 0, n_rec = 0;
+    for (int b = 0; b < nb; ++b) {
+      const int cur = b & 1;
+      named_sync(kBarReady + cur);
+      const int nvalid = bad ? 0 : (int)(moves - (long long)b * 32 < 32 ? moves - (long long)b * 32 : 32);
+      uint32_t acc_cur = 0;
+      const int4* R4 = reinterpret_cast<const int4*>(rec + cur * 32);
+      // records are read one move ahead, before the stores of the current move
+      int4 nxt[kWords];
+      if (nvalid > 0) {
+#pragma unroll
+        for (int q = 0; q < kWords; ++q) nxt[q] = R4[q];
+      }
+      for (int k = 0; k < nvalid; ++k) {
+        Rec<kTraj> r;
+        memcpy(&r, nxt, sizeof r);
+        if (k + 1 < nvalid) {
+#pragma unroll
+          for (int q = 0; q < kWords; ++q) nxt[q] = R4[(k + 1) * kWords + q];
+        }
+        const uint32_t need = (r.cprev & acc_prev) | (r.ccur & acc_cur);
+        const int site = r.site;
+        bool acc;
+        if constexpr (kTraj) {
+          double dE = r.dE;
+          if (need) {
+            __syncwarp();
+            int X, Y, Z;
+            bcc_coords(site, L, a.geo.divL, X, Y, Z);
+            double dn = 0.0;
+            if (lane == 0)
+              dn = (double)delta_energy<true>(a, off_s, J_s, sx, sy, sz, site, X, Y, Z, r.nx, r.ny, r.nz, 0, 1, 1u);
+            dE = __shfl_sync(kFullMask, dn, 0);
+            ++n_rec;
+          }
+          const double Ep = __dadd_rn(E, dE);
+          const int bp = bin_fp64(Ep, a.win);
+          const int rel = bp - wlo;
+          acc = false;
+          if ((unsigned)rel < (unsigned)W) {
+            const double lngp = (bp == bcur) ? (double)lng_cur : (double)lng_s[rel];
+            const double d = __dsub_rn((double)lng_cur, lngp);
+            acc = (d >= 0.0) || (r.u < exp_fp64(d, a.ex));
+            if (acc) {
+              if (bp != bcur) {
+                lng_s[bcur - wlo] = lng_cur;
+                H_s[bcur - wlo] = h_cur;
+                lng_cur = (Lng)lngp;
+                h_cur = H_s[rel];
+                bcur = bp;
+              }
+              E = Ep;
+            }
+          }
+        } else {
+          int dq = r.dq;
+          if (need) {
+            __syncwarp();
+            int X, Y, Z;
+            bcc_coords(site, L, a.geo.divL, X, Y, Z);
+            const float dEn = (float)delta_energy<false>(a, off_s, J_s, sx, sy, sz, site, X, Y, Z, r.nx, r.ny, r.nz,
+                                                         lane, 32, kFullMask);
+            dq = dq24_of(dEn, a.win);
+            ++n_rec;
+          }
+          const long long Ep = Efx + ((long long)dq << 8);
+          const int bp = fx_bin(Ep);
+          const int db = bp - bcur;
+          if (db == 0) {
+            acc = true;                      // same bin: ln g ratio 1
+          } else {
+            const int rel = bp - wlo;
+            acc = false;
+            if ((unsigned)rel < (unsigned)W) {
+              const long long lngp = db == 1 ? lng_p : (db == -1 ? lng_m : (long long)lng_s[rel]);
+              const long long d = (long long)lng_cur - lngp;
+              const int d20 = d < -(1LL << 51) ? (int)0x80000000 : (int)(d >> 20);
+              acc = d >= 0 || r.lu < d20;
+              if (acc) {
+                lng_s[bcur - wlo] = lng_cur;
+                H_s[bcur - wlo] = h_cur;
+                if (db == 1) {
+                  lng_m = (long long)lng_cur;
+                } else if (db == -1) {
+                  lng_p = (long long)lng_cur;
+                }
+                lng_cur = (Lng)lngp;
+                h_cur = H_s[rel];
+                bcur = bp;
+                if (db != -1) lng_p = bcur + 1 < wlo + W ? (long long)lng_s[bcur + 1 - wlo] : 0;
+                if (db != 1) lng_m = bcur - 1 >= wlo ? (long long)lng_s[bcur - 1 - wlo] : 0;
+              }
+            }
+          }
+          if (acc) Efx = Ep;
+        }
+        if (acc) {
+          acc_cur |= 1u << k;
+          ++n_acc;
+          if (lane == 0) {
+            sx[site] = r.nx;
+            sy[site] = r.ny;
+            sz[site] = r.nz;
+          }
+        }
+        if (!frozen) {
+          if constexpr (kTraj)
+            lng_cur = (Lng)__dadd_rn((double)lng_cur, lnf);
+          else
+            lng_cur = (Lng)((long long)lng_cur + lnf_fx);
+          ++h_cur;
+        }
+      }
+      acc_prev = acc_cur;
+      __syncwarp();
+      named_arrive(kBarDone + cur);
+    }
+    if (lane == 0 && !bad) {
+      if constexpr (kTraj) {
+        a.st.E[slot] = E;
+        a.st.bin[slot] = bcur;
+      } else {
+        a.st.efx[slot] = Efx;
+      }
+      lng_s[bcur - wlo] = lng_cur;
+      H_s[bcur - wlo] = h_cur;
+      a.st.steps[slot] = t0 + moves;
+      a.st.accepts[slot] += n_acc;
+      a.st.recomputes[slot] += n_rec;
+    }
+   } else {
+    // ------------------------ resolver (production mode) ------------------------
+    // Current bin: its ln g and H live in registers (lng_now, h_now) and are written back only
+    // when the walker leaves the bin; ln g of the two neighbouring bins is cached (lng_m, lng_p).
+    long long Efx = a.st.efx[slot];
+    int bcur = fx_bin(Efx);
+    const long long lnf_fx = a.st.lnf_fx[slot];
+    const bool frozen = !((double)lnf_fx * kLngUnit >= a.lnf_final);
+    const long long lnf_eff = frozen ? 0 : lnf_fx;
+    const uint32_t hinc = frozen ? 0u : 1u;
+    const bool bad = (unsigned)(bcur - wlo) >= (unsigned)W;
+    if (bad && lane == 0) atomicExch(a.st.ctrl + 0, kErrOutOfWindow);
+    long long lng_in = bad ? 0 : (long long)lng_s[bcur - wlo];
+    uint32_t h_in = bad ? 0u : H_s[bcur - wlo];
+    long long lng_m = 0, lng_p = 0;
+    if (!bad) {
+      lng_m = bcur - 1 >= wlo ? (long long)lng_s[bcur - 1 - wlo] : 0;
+      lng_p = bcur + 1 < wlo + W ? (long long)lng_s[bcur + 1 - wlo] : 0;
+    }
+    // segment state: the walker entered bcur (or the batch began) at move k_seg with ln g = lng_seg
+    // and histogram h_seg; after j more moves there, ln g = lng_seg + j ln f
+    long long lng_seg = lng_in;
+    uint32_t h_seg = h_in;
+    uint32_t acc_prev = 0;
+    int n_rec = 0;
+    long long n_acc = 0;
+    for (int b = 0; b < nb; ++b) {
+      const int cur = b & 1;
+      named_sync(kBarReady + cur);
+      const int nvalid = bad ? 0 : (int)(moves - (long long)b * 32 < 32 ? moves - (long long)b * 32 : 32);
+      int k_seg = 0;
+      uint32_t acc_cur = 0, stored = 0;
+      const int4* R4 = reinterpret_cast<const int4*>(rec + cur * 32);
+      // ---- parallel part: lane = move index ----
+      const Rec<false>& mine = rec[cur * 32 + lane];
+      const int my_lu = mine.lu;
+      const uint32_t need_prev = __ballot_sync(kFullMask, lane < nvalid && (mine.cprev & acc_prev) != 0u);
+      // would a step to bcur + 1 / bcur - 1 be accepted at this move, given no change of bin since k_seg
+      auto pass_masks = [&](uint32_t& up, uint32_t& down) {
+        const long long ln = lng_seg + (long long)(lane - k_seg) * lnf_eff;
+        const long long du = ln - lng_p, dd = ln - lng_m;
+        const int u20 = du < -(1LL << 51) ? (int)0x80000000 : (int)(du >> 20);
+        const int l20 = dd < -(1LL << 51) ? (int)0x80000000 : (int)(dd >> 20);
+        const bool pu = bcur + 1 < wlo + W && (du >= 0 || my_lu < u20);
+        const bool pd = bcur - 1 >= wlo && (dd >= 0 || my_lu < l20);
+        up = __ballot_sync(kFullMask, pu);
+        down = __ballot_sync(kFullMask, pd);
+      };
+      uint32_t up_mask, down_mask;
+      pass_masks(up_mask, down_mask);
+      int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
+      if (nvalid > 0) {
+        n0 = R4[0];
+        n1 = R4[1];
+      }
+      // ---- sequential part ----
+      for (int k = 0; k < nvalid; ++k) {
+        const int4 r0 = n0, r1 = n1;  // dq (x, y), lu (z), cprev (w) | ccur (x), site (y), nx, ny
+        if (k + 1 < nvalid) {
+          n0 = R4[3 * (k + 1)];
+          n1 = R4[3 * (k + 1) + 1];
+        }
+        long long dq = (long long)(((unsigned long long)(uint32_t)r0.y << 32) | (uint32_t)r0.x);
+        const uint32_t bit = 1u << k;
+        const bool need = ((need_prev & bit) | ((uint32_t)r1.x & acc_cur)) != 0u;
+        long long Ep = Efx + dq;
+        int db = fx_bin(Ep) - bcur;
+        const bool pass = db == 1 ? (up_mask & bit) != 0u : (db == -1 ? (down_mask & bit) != 0u : db != 0);
+        if (!(need | pass)) {
+          // same bin (accepted) or a rejected step to a neighbouring bin
+          Efx = db == 0 ? Ep : Efx;
+          acc_cur |= db == 0 ? bit : 0u;
+          continue;
+        }
+        // ---- rare: re-evaluation, a jump of two or more bins, or an accepted change of bin ----
+        if (need) {
+          // publish the accepted spins of this batch, then re-evaluate on the current lattice
+          const uint32_t pend = acc_cur & ~stored;
+          if ((pend >> lane) & 1u) {
+            sx[mine.site] = mine.nx;
+            sy[mine.site] = mine.ny;
+            sz[mine.site] = mine.nz;
+          }
+          stored |= pend;
+          __syncwarp();
+          const int site = r1.y;
+          int X, Y, Z;
+          bcc_coords(site, L, a.geo.divL, X, Y, Z);
+          const float dEn = delta_energy<false>(a, off_s, J_s, sx, sy, sz, site, X, Y, Z, __int_as_float(r1.z),
+                                               __int_as_float(r1.w), rec[cur * 32 + k].nz, lane, 32, kFullMask);
+          dq = (long long)dq24_of(dEn, a.win) << 8;
+          ++n_rec;
+          Ep = Efx + dq;
+          db = fx_bin(Ep) - bcur;
+        }
+        const int bp = bcur + db;
+        const long long lng_now = lng_seg + (long long)(k - k_seg) * lnf_eff;
+        bool acc;
+        if (db == 0) {
+          acc = true;
+        } else {
+          const int rel = bp - wlo;
+          acc = false;
+          if ((unsigned)rel < (unsigned)W) {
+            const long long lngp = db == 1 ? lng_p : (db == -1 ? lng_m : (long long)lng_s[rel]);
+            const long long d = lng_now - lngp;
+            const int e20 = d < -(1LL << 51) ? (int)0x80000000 : (int)(d >> 20);
+            acc = d >= 0 || r0.z < e20;
+            if (acc) {
+              // leave bcur: write it back, shift the neighbour cache, start a new segment
+              lng_s[bcur - wlo] = (Lng)lng_now;
+              H_s[bcur - wlo] = h_seg + hinc * (uint32_t)(k - k_seg);
+              if (db == 1) lng_m = lng_now;
+              if (db == -1) lng_p = lng_now;
+              lng_seg = lngp;
+              h_seg = H_s[rel];
+              k_seg = k;
+              bcur = bp;
+              if (db != -1) lng_p = bcur + 1 < wlo + W ? (long long)lng_s[bcur + 1 - wlo] : 0;
+              if (db != 1) lng_m = bcur - 1 >= wlo ? (long long)lng_s[bcur - 1 - wlo] : 0;
+              pass_masks(up_mask, down_mask);
+            }
+          }
+        }
+        if (acc) {
+          Efx = Ep;
+          acc_cur |= bit;
+        }
+      }
+      // the batch's moves at the current bin
+      lng_seg += (long long)(nvalid - k_seg) * lnf_eff;
+      h_seg += hinc * (uint32_t)(nvalid - k_seg);
+      // accepted spins not yet written (no two share a site: a second one would have been
+      // re-evaluated, which publishes the first)
+      const uint32_t pend = acc_cur & ~stored;
+      if ((pend >> lane) & 1u) {
+        sx[mine.site] = mine.nx;
+        sy[mine.site] = mine.ny;
+        sz[mine.site] = mine.nz;
+      }
+      n_acc += __popc(acc_cur);
+      acc_prev = acc_cur;
+      __syncwarp();
+      named_arrive(kBarDone + cur);
+    }
+    if (lane == 0 && !bad) {
+      a.st.efx[slot] = Efx;
+      lng_s[bcur - wlo] = (Lng)lng_seg;
+      H_s[bcur - wlo] = h_seg;
+      a.st.steps[slot] = t0 + moves;
+      a.st.accepts[slot] += n_acc;
+      a.st.recomputes[slot] += n_rec;
+    }
+   }
+  }
+  __syncthreads();
+
+  if (kSmem)
+    for (size_t i = tid; i < 3 * (size_t)N; i += blockDim.x) gsp[i] = spin_s[i];
+  for (int w = tid; w < W; w += blockDim.x) {
+    if constexpr (kTraj)
+      a.st.lng[lbase + w] = (double)lng_s[w];
+    else
+      a.st.lng_fx[lbase + w] = (long long)lng_s[w];
+    a.st.H[lbase + w] = H_s[w];
+  }
+  if (a.recompute) {
+    const double Ef = full_energy<kTraj>(a, off_s, sx, sy, sz, red);
+    if (tid == 0) {
+      if constexpr (kTraj) {
+        const double d = fabs(Ef - a.st.E[slot]);
+        if (d > a.st.drift[slot]) a.st.drift[slot] = d;
+      } else {
+        const long long efx = a.st.efx[slot];
+        const double Er = a.win.e_min + a.win.dE * ((double)efx / kEnergyScale);
+        const double d = fabs(Ef - Er);
+        if (d > a.st.drift[slot]) a.st.drift[slot] = d;
+        long long nf = __double2ll_rn((Ef - a.win.e_min) / a.win.dE * kEnergyScale);
+        const long long lo_fx = (long long)wlo << 32;
+        const long long hi_fx = ((long long)(wlo + W) << 32) - 1;
+        nf = nf < lo_fx ? lo_fx : (nf > hi_fx ? hi_fx : nf);
+        a.st.efx[slot] = nf;
+      }
+    }
+  }
+}
+
+size_t walker_pipe_smem_bytes(bool traj, bool smem_lattice, int N, int W, int own_entries) {
+  const size_t lng = align16((traj ? sizeof(double) : sizeof(long long)) * (size_t)W);
+  const size_t h = align16((size_t)W * 4);
+  const size_t real = traj ? sizeof(double) : sizeof(float);
+  const size_t recs = (traj ? sizeof(Rec<true>) : sizeof(Rec<false>)) * 64;
+  size_t bytes = lng + h + 4 * kMaxSlotsPerSite + real * kMaxSlotsPerSite + recs + 8 * (size_t)own_entries;
+  if (smem_lattice) bytes += real * 3 * (size_t)N;
+  return bytes;
+}
+
+template <bool kTraj, bool kSmem, int NSH>
+static cudaError_t launch_pipe_t(const WalkerArgs& a, int n_slots, size_t smem, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(walker_pipe_kernel<kTraj, kSmem, NSH>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  walker_pipe_kernel<kTraj, kSmem, NSH><<<n_slots, kWalkerThreads, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool kTraj, bool kSmem>
+static cudaError_t launch_pipe_shells(const WalkerArgs& a, int n_slots, size_t smem, cudaStream_t stream) {
+  switch (a.geo.n_shells) {
+    case 1: return launch_pipe_t<kTraj, kSmem, 1>(a, n_slots, smem, stream);
+    case 2: return launch_pipe_t<kTraj, kSmem, 2>(a, n_slots, smem, stream);
+    case 3: return launch_pipe_t<kTraj, kSmem, 3>(a, n_slots, smem, stream);
+    case 4: return launch_pipe_t<kTraj, kSmem, 4>(a, n_slots, smem, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_walkers_pipe(const WalkerArgs& a, int n_slots, bool traj, bool smem_lattice, size_t smem,
+                                cudaStream_t stream) {
+  if (traj) {
+    return smem_lattice ? launch_pipe_shells<true, true>(a, n_slots, smem, stream)
+                        : launch_pipe_shells<true, false>(a, n_slots, smem, stream);
+  }
+  return smem_lattice ? launch_pipe_shells<false, true>(a, n_slots, smem, stream)
+                      : launch_pipe_shells<false, false>(a, n_slots, smem, stream);
+}
+
+}  // namespace rewl

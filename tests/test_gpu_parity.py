@@ -31,6 +31,7 @@ def run_both(gpu, orc, intervals):
 @pytest.mark.parametrize("G", [1, 2, 4, 8, 16, 32])
 def test_cfg1_every_group_size(G):
     gpu, orc = make_pair(group_size=G, exchange_interval=1000, **CFG1)
+    assert gpu.info()["pipelined"] == (1 if G == 1 else 0)
     run_both(gpu, orc, 6)
     gpu.close()
 
@@ -94,7 +95,7 @@ def test_cfg2_size_shared_lattice():
     """bcc L=16 (8192 spins), 16 windows x 4 walkers, 2000 bins: the production workload's geometry."""
     gpu, orc = make_pair(group_size=1, L=16, J=(1.0, 0.5), n_bins=2000, n_windows=16, walkers_per_window=4,
                          overlap=0.75, flatness=0.8, lnf_final=1e-8, seed=1, exchange_interval=3000)
-    assert gpu.info()["lattice_in_shared"] == 1
+    assert gpu.info()["lattice_in_shared"] == 1 and gpu.info()["pipelined"] == 1
     run_both(gpu, orc, 2)
     gpu.close()
 
@@ -103,7 +104,7 @@ def test_global_memory_lattice_path():
     """bcc L=20 in FP64 (384 KB per lattice) does not fit in shared memory: global-memory path."""
     gpu, orc = make_pair(group_size=1, L=20, J=(1.0, 0.5), n_bins=400, n_windows=3, walkers_per_window=1,
                          overlap=0.75, flatness=0.8, lnf_final=1e-8, seed=2, exchange_interval=2000)
-    assert gpu.info()["lattice_in_shared"] == 0
+    assert gpu.info()["lattice_in_shared"] == 0 and gpu.info()["pipelined"] == 1
     run_both(gpu, orc, 2)
     gpu.close()
 
@@ -119,3 +120,22 @@ def test_frozen_walkers_and_set_initial_lng():
     w = gpu.walkers()
     assert np.all(w["H"] == 0)
     gpu.close()
+
+
+def test_pipelined_walker_tiny_lattice_heavy_conflicts():
+    """bcc L=3 (54 spins): nearly every move of a 64-move window conflicts; still bit-exact."""
+    gpu, orc = make_pair(group_size=1, L=3, J=(1.0,), n_bins=60, n_windows=2, walkers_per_window=2,
+                         overlap=0.75, flatness=0.8, lnf_final=1e-3, seed=21, exchange_interval=4000)
+    assert gpu.info()["pipelined"] == 1
+    run_both(gpu, orc, 3)
+    gpu.close()
+
+
+def test_pipelined_walker_partial_batches():
+    """Exchange intervals of 1, 31, 33 and 65 moves (partial final batches, one- and two-batch runs)."""
+    for ex in (1, 31, 33, 65):
+        gpu, orc = make_pair(group_size=1, L=5, J=(1.0, 0.5, 0.25), n_bins=100, n_windows=3,
+                             walkers_per_window=2, overlap=0.75, flatness=0.8, lnf_final=1e-3, seed=ex,
+                             exchange_interval=ex)
+        run_both(gpu, orc, 4)
+        gpu.close()
