@@ -489,7 +489,6 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const Walke
       const int nvalid = bad ? 0 : (int)(moves - (long long)b * 32 < 32 ? moves - (long long)b * 32 : 32);
       int k_seg = 0;
       uint32_t acc_cur = 0, stored = 0;
-      const int4* R4 = reinterpret_cast<const int4*>(rec + cur * 32);
       // ---- parallel part: lane = move index ----
       const Rec<false>& mine = rec[cur * 32 + lane];
       const int my_lu = mine.lu;
@@ -507,85 +506,121 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const Walke
       };
       uint32_t up_mask, down_mask;
       pass_masks(up_mask, down_mask);
-      int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
-      if (nvalid > 0) {
-        n0 = R4[0];
-        n1 = R4[1];
-      }
-      // ---- sequential part ----
-      for (int k = 0; k < nvalid; ++k) {
-        const int4 r0 = n0, r1 = n1;  // dq (x, y), lu (z), cprev (w) | ccur (x), site (y), nx, ny
-        if (k + 1 < nvalid) {
-          n0 = R4[3 * (k + 1)];
-          n1 = R4[3 * (k + 1) + 1];
+      // ---- sequential part, in branch-free blocks of 8 moves ----
+      // Within a bin the state is frac = Efx - (bcur << 32) in [0, 2^32).  A move in the same bin is
+      // accepted (frac += dq); a step to a neighbouring bin is accepted iff its pass bit is set, an
+      // event handled out of line, like re-evaluations and jumps of two or more bins.  The common
+      // path uses no compare-and-select: masks come from sign bits.
+      const long long my_dq = mine.dq;
+      const uint32_t my_ccur = mine.ccur;
+      uint32_t frac = (uint32_t)Efx;
+      int k = 0;
+      while (k < nvalid) {
+        const uint32_t frac0 = frac, acc0 = acc_cur;
+        uint32_t exc = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int kk = k + u;
+          const uint32_t lo = (uint32_t)__shfl_sync(kFullMask, (int)(uint32_t)my_dq, kk & 31);
+          const int hi = __shfl_sync(kFullMask, (int)(my_dq >> 32), kk & 31);
+          const uint32_t cc = (uint32_t)__shfl_sync(kFullMask, (int)my_ccur, kk & 31);
+          const uint32_t vmask = (uint32_t)((kk - nvalid) >> 31);          // all ones while kk < nvalid
+          const uint32_t bit = (1u << (kk & 31)) & vmask;
+          const uint32_t t_lo = frac + lo;
+          const uint32_t carry = ((frac & lo) | ((frac | lo) & ~t_lo)) >> 31;
+          const int th = hi + (int)carry;                                     // high word of frac + dq: bins moved
+          const uint32_t nz = (uint32_t)((th | -th) >> 31);                   // all ones iff th != 0
+          const uint32_t stay = ~nz & vmask;
+          frac = (t_lo & stay) | (frac & ~stay);
+          acc_cur |= bit & stay;
+          const uint32_t up = (uint32_t)(((th - 1) | (1 - th)) >> 31);       // all ones iff th != 1
+          const uint32_t dn = (uint32_t)(((th + 1) | (-1 - th)) >> 31);      // all ones iff th != -1
+          const uint32_t far = nz & up & dn;                                  // |th| >= 2
+          const uint32_t need = (need_prev & bit) | (cc & acc_cur & ~bit);
+          exc |= bit & (((~up) & up_mask) | ((~dn) & down_mask) | far | (need ? 0xffffffffu : 0u));
         }
-        long long dq = (long long)(((unsigned long long)(uint32_t)r0.y << 32) | (uint32_t)r0.x);
-        const uint32_t bit = 1u << k;
-        const bool need = ((need_prev & bit) | ((uint32_t)r1.x & acc_cur)) != 0u;
-        long long Ep = Efx + dq;
-        int db = fx_bin(Ep) - bcur;
-        const bool pass = db == 1 ? (up_mask & bit) != 0u : (db == -1 ? (down_mask & bit) != 0u : db != 0);
-        if (!(need | pass)) {
-          // same bin (accepted) or a rejected step to a neighbouring bin
-          Efx = db == 0 ? Ep : Efx;
-          acc_cur |= db == 0 ? bit : 0u;
+        if (exc == 0u) {
+          k += 8;
           continue;
         }
-        // ---- rare: re-evaluation, a jump of two or more bins, or an accepted change of bin ----
-        if (need) {
-          // publish the accepted spins of this batch, then re-evaluate on the current lattice
-          const uint32_t pend = acc_cur & ~stored;
-          if ((pend >> lane) & 1u) {
-            sx[mine.site] = mine.nx;
-            sy[mine.site] = mine.ny;
-            sz[mine.site] = mine.nz;
+        // first exceptional move: replay the block up to it, then handle it in full
+        const int kx = __ffs(exc) - 1;
+        frac = frac0;
+        acc_cur = acc0;
+        for (int kk = k; kk < kx; ++kk) {
+          const uint32_t lo = (uint32_t)__shfl_sync(kFullMask, (int)(uint32_t)my_dq, kk);
+          const int hi = __shfl_sync(kFullMask, (int)(my_dq >> 32), kk);
+          const uint32_t t_lo = frac + lo;
+          const int th = hi + (int)(t_lo < frac);
+          if (th == 0) {
+            frac = t_lo;
+            acc_cur |= 1u << kk;
           }
-          stored |= pend;
-          __syncwarp();
-          const int site = r1.y;
-          int X, Y, Z;
-          bcc_coords(site, L, a.geo.divL, X, Y, Z);
-          const float dEn = delta_energy<false>(a, off_s, J_s, sx, sy, sz, site, X, Y, Z, __int_as_float(r1.z),
-                                               __int_as_float(r1.w), rec[cur * 32 + k].nz, lane, 32, kFullMask);
-          dq = (long long)dq24_of(dEn, a.win) << 8;
-          ++n_rec;
-          Ep = Efx + dq;
-          db = fx_bin(Ep) - bcur;
         }
-        const int bp = bcur + db;
-        const long long lng_now = lng_seg + (long long)(k - k_seg) * lnf_eff;
-        bool acc;
-        if (db == 0) {
-          acc = true;
-        } else {
-          const int rel = bp - wlo;
-          acc = false;
-          if ((unsigned)rel < (unsigned)W) {
-            const long long lngp = db == 1 ? lng_p : (db == -1 ? lng_m : (long long)lng_s[rel]);
-            const long long d = lng_now - lngp;
-            const int e20 = d < -(1LL << 51) ? (int)0x80000000 : (int)(d >> 20);
-            acc = d >= 0 || r0.z < e20;
-            if (acc) {
-              // leave bcur: write it back, shift the neighbour cache, start a new segment
-              lng_s[bcur - wlo] = (Lng)lng_now;
-              H_s[bcur - wlo] = h_seg + hinc * (uint32_t)(k - k_seg);
-              if (db == 1) lng_m = lng_now;
-              if (db == -1) lng_p = lng_now;
-              lng_seg = lngp;
-              h_seg = H_s[rel];
-              k_seg = k;
-              bcur = bp;
-              if (db != -1) lng_p = bcur + 1 < wlo + W ? (long long)lng_s[bcur + 1 - wlo] : 0;
-              if (db != 1) lng_m = bcur - 1 >= wlo ? (long long)lng_s[bcur - 1 - wlo] : 0;
-              pass_masks(up_mask, down_mask);
+        Efx = ((long long)bcur << 32) | frac;
+        {
+          const int kk = kx;
+          const Rec<false>& rk = rec[cur * 32 + kk];
+          long long dq = rk.dq;
+          const uint32_t bit = 1u << kk;
+          const bool need = ((need_prev & bit) | (rk.ccur & acc_cur)) != 0u;
+          if (need) {
+            // publish the accepted spins of this batch, then re-evaluate on the current lattice
+            const uint32_t pend = acc_cur & ~stored;
+            if ((pend >> lane) & 1u) {
+              sx[mine.site] = mine.nx;
+              sy[mine.site] = mine.ny;
+              sz[mine.site] = mine.nz;
+            }
+            stored |= pend;
+            __syncwarp();
+            int X, Y, Z;
+            bcc_coords(rk.site, L, a.geo.divL, X, Y, Z);
+            const float dEn = delta_energy<false>(a, off_s, J_s, sx, sy, sz, rk.site, X, Y, Z, rk.nx, rk.ny, rk.nz,
+                                                 lane, 32, kFullMask);
+            dq = (long long)dq24_of(dEn, a.win) << 8;
+            ++n_rec;
+          }
+          const long long Ep = Efx + dq;
+          const int db = fx_bin(Ep) - bcur;
+          const int bp = bcur + db;
+          const long long lng_now = lng_seg + (long long)(kk - k_seg) * lnf_eff;
+          bool acc;
+          if (db == 0) {
+            acc = true;
+          } else {
+            const int rel = bp - wlo;
+            acc = false;
+            if ((unsigned)rel < (unsigned)W) {
+              const long long lngp = db == 1 ? lng_p : (db == -1 ? lng_m : (long long)lng_s[rel]);
+              const long long d = lng_now - lngp;
+              const int e20 = d < -(1LL << 51) ? (int)0x80000000 : (int)(d >> 20);
+              acc = d >= 0 || rk.lu < e20;
+              if (acc) {
+                // leave bcur: write it back, shift the neighbour cache, start a new segment
+                lng_s[bcur - wlo] = (Lng)lng_now;
+                H_s[bcur - wlo] = h_seg + hinc * (uint32_t)(kk - k_seg);
+                if (db == 1) lng_m = lng_now;
+                if (db == -1) lng_p = lng_now;
+                lng_seg = lngp;
+                h_seg = H_s[rel];
+                k_seg = kk;
+                bcur = bp;
+                if (db != -1) lng_p = bcur + 1 < wlo + W ? (long long)lng_s[bcur + 1 - wlo] : 0;
+                if (db != 1) lng_m = bcur - 1 >= wlo ? (long long)lng_s[bcur - 1 - wlo] : 0;
+                pass_masks(up_mask, down_mask);
+              }
             }
           }
+          if (acc) {
+            Efx = Ep;
+            acc_cur |= bit;
+          }
+          frac = (uint32_t)Efx;
         }
-        if (acc) {
-          Efx = Ep;
-          acc_cur |= bit;
-        }
+        k = kx + 1;
       }
+      Efx = ((long long)bcur << 32) | frac;
       // the batch's moves at the current bin
       lng_seg += (long long)(nvalid - k_seg) * lnf_eff;
       h_seg += hinc * (uint32_t)(nvalid - k_seg);
