@@ -184,6 +184,10 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const Walke
   p += sizeof(Real) * kMaxSlotsPerSite;
   Rec<kTraj>* rec = reinterpret_cast<Rec<kTraj>*>(p);
   p += sizeof(Rec<kTraj>) * 64;
+  int4* pk = reinterpret_cast<int4*>(p);          // production: {dq lo, dq hi, ccur, -} per move
+  p += sizeof(int4) * 64;
+  uint32_t* fhist = reinterpret_cast<uint32_t*>(p);  // production: energy fraction before each move
+  p += sizeof(uint32_t) * 32;
   uint2* own = reinterpret_cast<uint2*>(p);
   p += sizeof(uint2) * ((size_t)omask + 1);
   Real* spin_s = reinterpret_cast<Real*>(p);
@@ -277,6 +281,10 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const Walke
       }
       r.cprev = b > 0 ? oprev : 0u;
       r.ccur = ocur & ((1u << lane) - 1u);
+      if constexpr (!kTraj) {
+        const unsigned long long dqu = (unsigned long long)r.dq;
+        pk[cur * 32 + lane] = make_int4((int)(uint32_t)dqu, (int)(uint32_t)(dqu >> 32), (int)r.ccur, 0);
+      }
       r.site = site;
       r.nx = nx;
       r.ny = ny;
@@ -511,19 +519,22 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const Walke
       // accepted (frac += dq); a step to a neighbouring bin is accepted iff its pass bit is set, an
       // event handled out of line, like re-evaluations and jumps of two or more bins.  The common
       // path uses no compare-and-select: masks come from sign bits.
-      const long long my_dq = mine.dq;
-      const uint32_t my_ccur = mine.ccur;
+      const int4* P4 = pk + cur * 32;
       uint32_t frac = (uint32_t)Efx;
       int k = 0;
       while (k < nvalid) {
-        const uint32_t frac0 = frac, acc0 = acc_cur;
+        const uint32_t acc0 = acc_cur;
         uint32_t exc = 0;
+        int4 q[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) q[u] = P4[(k + u) & 31];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int kk = k + u;
-          const uint32_t lo = (uint32_t)__shfl_sync(kFullMask, (int)(uint32_t)my_dq, kk & 31);
-          const int hi = __shfl_sync(kFullMask, (int)(my_dq >> 32), kk & 31);
-          const uint32_t cc = (uint32_t)__shfl_sync(kFullMask, (int)my_ccur, kk & 31);
+          if (lane == u) fhist[u] = frac;
+          const uint32_t lo = (uint32_t)q[u].x;
+          const int hi = q[u].y;
+          const uint32_t cc = (uint32_t)q[u].z;
           const uint32_t vmask = (uint32_t)((kk - nvalid) >> 31);          // all ones while kk < nvalid
           const uint32_t bit = (1u << (kk & 31)) & vmask;
           const uint32_t t_lo = frac + lo;
@@ -543,20 +554,11 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const Walke
           k += 8;
           continue;
         }
-        // first exceptional move: replay the block up to it, then handle it in full
+        // first exceptional move: the block's moves before it stand; restore the state there
         const int kx = __ffs(exc) - 1;
-        frac = frac0;
-        acc_cur = acc0;
-        for (int kk = k; kk < kx; ++kk) {
-          const uint32_t lo = (uint32_t)__shfl_sync(kFullMask, (int)(uint32_t)my_dq, kk);
-          const int hi = __shfl_sync(kFullMask, (int)(my_dq >> 32), kk);
-          const uint32_t t_lo = frac + lo;
-          const int th = hi + (int)(t_lo < frac);
-          if (th == 0) {
-            frac = t_lo;
-            acc_cur |= 1u << kk;
-          }
-        }
+        __syncwarp();
+        frac = fhist[kx - k];
+        acc_cur = acc0 | (acc_cur & ((1u << kx) - 1u));
         Efx = ((long long)bcur << 32) | frac;
         {
           const int kk = kx;
@@ -683,7 +685,7 @@ size_t walker_pipe_smem_bytes(bool traj, bool smem_lattice, int N, int W, int ow
   const size_t lng = align16((traj ? sizeof(double) : sizeof(long long)) * (size_t)W);
   const size_t h = align16((size_t)W * 4);
   const size_t real = traj ? sizeof(double) : sizeof(float);
-  const size_t recs = (traj ? sizeof(Rec<true>) : sizeof(Rec<false>)) * 64;
+  const size_t recs = (traj ? sizeof(Rec<true>) : sizeof(Rec<false>)) * 64 + sizeof(int4) * 64 + sizeof(uint32_t) * 32;
   size_t bytes = lng + h + 4 * kMaxSlotsPerSite + real * kMaxSlotsPerSite + recs + 8 * (size_t)own_entries;
   if (smem_lattice) bytes += real * 3 * (size_t)N;
   return bytes;
