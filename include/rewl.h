@@ -194,6 +194,24 @@ rewl_status rewl_stitch_device(const double* frag, const int32_t* starts_host, i
                                int walkers_per_window, int window_bins, int n_bins, double* out,
                                int32_t* bstar_out, void* cuda_stream);
 
+/* No-allocation variant of rewl_stitch_device.  The paper has no counterpart: this entry point
+ * serves callers that must not allocate device memory, such as a host application that reserves
+ * all device memory up front, or a latency-critical loop that must not trigger the implicit device
+ * synchronisation of cudaMalloc / cudaFree.  Same arguments, layout, rules and result as
+ * rewl_stitch_device (all pointers device memory except starts_host).
+ * Scratch: one statically sized device array inside the library, 4 MiB (4194304 bytes), held by
+ * every GPU that loads the library until the process exits.  The call needs
+ * 8*h*W + 4*h + 4*max(h-1,1) bytes (each of the three parts rounded up to 256); larger sizes
+ * return REWL_EINVAL.  The first call on a device looks up the array's device address for that
+ * device (with it current); make that first call before any stream capture.  Every call shares the
+ * one array and leaves its contents behind (each call writes all the scratch it reads), so calls
+ * whose work overlaps on the GPU -- different streams or host threads -- race.  The call
+ * synchronises cuda_stream before returning and makes no cudaMalloc, cudaFree or other allocation.
+ * Errors are reported by rewl_last_error(NULL). */
+rewl_status rewl_stitch_device_noalloc(const double* frag, const int32_t* starts_host, int n_windows,
+                                       int walkers_per_window, int window_bins, int n_bins, double* out,
+                                       int32_t* bstar_out, void* cuda_stream);
+
 /* Thermodynamics from ln g (Sec. 4.1, Eq. 2-3, k_B = 1): for every T, the mean energy U(T),
  * the specific heat per spin C(T) = (<E^2> - <E>^2) / (N T^2) and ln Z(T).  All arrays host:
  * lng, e_centres [n_bins]; T, U_out, C_out, lnZ_out [n_T] (outputs may be NULL). Computed on

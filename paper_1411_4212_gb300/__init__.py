@@ -113,6 +113,7 @@ def load_library(path=LIB_PATH):
         "rewl_merge_lng": ([_vp, _vp, _vp], st),
         "rewl_merge_lng_device": ([_vp, _vp], st),
         "rewl_stitch_device": ([_vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp], st),
+        "rewl_stitch_device_noalloc": ([_vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp], st),
         "rewl_thermo": ([_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, _vp, _vp, _vp], st),
         "rewl_set_initial_lng": ([_vp, _vp, C.c_double], st),
         "rewl_get_info": ([_vp, C.POINTER(Info)], st),
@@ -368,6 +369,19 @@ def stitch_device(frag, starts, n_bins, out, bstar=None, stream=None):
     _check(lib.rewl_stitch_device(C.c_void_p(frag.data_ptr()), _ptr(st), h, m, W, int(n_bins),
                                   C.c_void_p(out.data_ptr()), None if bstar is None else C.c_void_p(bstar.data_ptr()),
                                   _stream_ptr(stream)))
+    return out
+
+
+def stitch_device_noalloc(frag, starts, n_bins, out, bstar=None, stream=None):
+    """Same as stitch_device, for callers that must not allocate device memory: the scratch is a
+    fixed 4 MiB device array inside the library (shared by all calls; see include/rewl.h)."""
+    lib = load_library()
+    h, m, W = frag.shape
+    st = np.ascontiguousarray(starts, dtype=np.int32)
+    _check(lib.rewl_stitch_device_noalloc(C.c_void_p(frag.data_ptr()), _ptr(st), h, m, W, int(n_bins),
+                                          C.c_void_p(out.data_ptr()),
+                                          None if bstar is None else C.c_void_p(bstar.data_ptr()),
+                                          _stream_ptr(stream)))
     return out
 
 

@@ -244,6 +244,8 @@ rewl_status check_ready(rewl_handle* h) {
 
 }  // namespace
 
+void rewl::set_handleless_error(const std::string& msg) { g_last_error = msg; }
+
 extern "C" {
 
 const char* rewl_last_error(const rewl_handle* h) {

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "rewl_types.h"
 
 namespace rewl {
@@ -56,5 +58,8 @@ cudaError_t launch_energies(const WalkerArgs& a, int n_replicas, bool traj, doub
 cudaError_t launch_neighbour_dump(const Geometry& g, int32_t* nbr, double* J, cudaStream_t stream);
 
 cudaError_t measure_smem_bandwidth(double* bytes_per_s, double* ms, cudaStream_t stream);
+
+// Message returned by rewl_last_error(NULL) (entry points without a handle).
+void set_handleless_error(const std::string& msg);
 
 }  // namespace rewl
