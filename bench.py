@@ -41,7 +41,7 @@ UNIT = "moves/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=40)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--intervals", type=int, default=20, help="exchange intervals per step")
@@ -100,11 +100,18 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def wait_first(self, timeout=10.0):
+        """Block until nvidia-smi has printed its first sample, so the timed region is covered."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.02)
+        self.lines.clear()
 
     def _read(self):
         for line in self.proc.stdout:
@@ -197,6 +204,39 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
+# DRAM traffic of the walker kernel, taken from the committed ncu summary of the same kernel.  The
+# summary records a hash of the kernel's sources; once they change the figure no longer applies and
+# the traffic is reported as null.
+PROFILE = os.path.join(ROOT, "profiles", "walker_pipe_cfg2.md")
+KERNEL_SOURCES = ["walker_pipe.cu", "walker_common.cuh", "device_common.cuh", "rewl_types.h"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1411_4212_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel, moves_per_launch):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled from the profiled launch."""
+    if not os.path.exists(PROFILE):
+        return None
+    fields = {}
+    for line in open(PROFILE):
+        if line.startswith("- ") and ": " in line:
+            k, v = line[2:].split(": ", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    try:
+        if fields["kernel"] != kernel or fields["source_sha256"] != kernel_source_hash():
+            return None
+        return float(fields["dram_bytes_per_launch"]) * moves_per_launch / float(fields["moves_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -235,6 +275,7 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
+    clocks.wait_first()
     step_ms, walk_ms = [], []
     barrier(world)
     torch.cuda.synchronize()
@@ -265,6 +306,9 @@ def main():
     achieved = bytes_per_move * S * WORKLOAD["exchange_interval"] / (walk_avg_ms * 1e-3)
     smem_peak, _ = rw.measure_smem_bandwidth(stream)
     walker_share = sum(walk_ms) / sum(step_ms)
+    pipelined = bool(sim.info()["pipelined"])
+    kernel = "walker_pipe_kernel<false,true,%d>" % len(WORKLOAD["J"]) if pipelined else "walker_kernel<false,true>"
+    traffic = profiled_traffic(kernel, S * WORKLOAD["exchange_interval"])
 
     # end to end through the public API with host buffers: ln g in (warm start), merged ln g out
     lng_in = np.zeros(B)
@@ -289,7 +333,6 @@ def main():
         cpu = cpu_baseline(args.cpu_seconds)
 
     if rank == 0:
-        peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -301,11 +344,13 @@ def main():
                        "group_size": sim.info()["group_size"], "accept_rate": acc_rate,
                        "recompute_rate": rec_rate},
             "roofline": {"bound": "smem", "achieved": achieved / 1e9, "peak": smem_peak / 1e9, "unit": "GB/s",
-                         "frac": achieved / smem_peak, "traffic": None,
-                         "kernel": "walker_kernel<false,true>", "bytes_per_move": bytes_per_move,
+                         "frac": achieved / smem_peak, "traffic": traffic,
+                         "kernel": kernel, "bytes_per_move": bytes_per_move,
                          "walker_ms_per_launch": walk_avg_ms, "walker_share_of_step": walker_share,
-                         "peak_source": "measured live: conflict-free 16-byte shared-memory loads on every SM"
-                                        + ("" if os.path.exists(peaks_path) else "")},
+                         "cycles_per_move_per_walker": walk_avg_ms * 1e-3 * (clk.get("sm_mhz") or 0) * 1e6
+                                                       / WORKLOAD["exchange_interval"],
+                         "sms_used": min(S, torch.cuda.get_device_properties(dev).multi_processor_count),
+                         "peak_source": "measured live: conflict-free 16-byte shared-memory loads on every SM"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (3 * I + 2),
             "clocks": clk,
