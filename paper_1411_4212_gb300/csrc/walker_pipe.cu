@@ -83,8 +83,8 @@ struct alignas(16) Rec<true> {
 };
 
 // Local field of (X, Y, Z) by one lane over all slots in canonical order, with the owner-table
-// words of the site's neighbours OR-ed into own0 / own1.
-template <bool kTraj, int NSH>
+// words of the site's neighbours OR-ed into own0 / own1 (kOwn).
+template <bool kTraj, int NSH, bool kOwn = true>
 __device__ __forceinline__ void field_one_lane(const typename Mode<kTraj>::Real* __restrict__ sx,
                                                const typename Mode<kTraj>::Real* __restrict__ sy,
                                                const typename Mode<kTraj>::Real* __restrict__ sz, int X, int Y, int Z,
@@ -132,9 +132,11 @@ __device__ __forceinline__ void field_one_lane(const typename Mode<kTraj>::Real*
       ty[T.sh[j]] += sy[n];
       tz[T.sh[j]] += sz[n];
     }
-    const uint2 o = own[n & omask];
-    own0 |= o.x;
-    own1 |= o.y;
+    if constexpr (kOwn) {
+      const uint2 o = own[n & omask];
+      own0 |= o.x;
+      own1 |= o.y;
+    }
   }
   if constexpr (!kTraj) {
 #pragma unroll
@@ -471,6 +473,9 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const Walke
     // when the walker leaves the bin; ln g of the two neighbouring bins is cached (lng_m, lng_p).
     long long Efx = a.st.efx[slot];
     int bcur = fx_bin(Efx);
+    float Jsh_r[4];
+#pragma unroll
+    for (int s2 = 0; s2 < 4; ++s2) Jsh_r[s2] = a.geo.Jsh_f[s2];
     const long long lnf_fx = a.st.lnf_fx[slot];
     const bool frozen = !((double)lnf_fx * kLngUnit >= a.lnf_final);
     const long long lnf_eff = frozen ? 0 : lnf_fx;
@@ -576,10 +581,23 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const Walke
             }
             stored |= pend;
             __syncwarp();
+            const int site = rk.site;
             int X, Y, Z;
-            bcc_coords(rk.site, L, a.geo.divL, X, Y, Z);
-            const float dEn = delta_energy<false>(a, off_s, J_s, sx, sy, sz, rk.site, X, Y, Z, rk.nx, rk.ny, rk.nz,
-                                                 lane, 32, kFullMask);
+            bcc_coords(site, L, a.geo.divL, X, Y, Z);
+            float dEn;
+            if constexpr (NSH <= 3) {
+              // up to 26 neighbours: every lane evaluates the same field with the producer's
+              // arithmetic (broadcast loads, no reduction across lanes)
+              float hx, hy, hz;
+              uint32_t o0 = 0, o1 = 0;
+              field_one_lane<false, NSH, false>(sx, sy, sz, X, Y, Z, L, Jsh_r, hx, hy, hz, own, omask, o0, o1);
+              const float dx = rk.nx - sx[site], dy = rk.ny - sy[site], dz = rk.nz - sz[site];
+              dEn = -fmaf(dz, hz, fmaf(dy, hy, dx * hx));
+            } else {
+              // 50 neighbours: spread over the lanes, reduced by shuffles
+              dEn = delta_energy<false>(a, off_s, J_s, sx, sy, sz, site, X, Y, Z, rk.nx, rk.ny, rk.nz, lane, 32,
+                                        kFullMask);
+            }
             dq = (long long)dq24_of(dEn, a.win) << 8;
             ++n_rec;
           }
