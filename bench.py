@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--intervals", type=int, default=20, help="exchange intervals per step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--workload", default="single", choices=["single", "batch64"],
+                   help="single: one job, bcc L=16 (the headline line); batch64: 64 jobs of bcc L=8..20 "
+                        "in one persistent launch")
     return p.parse_args()
 
 
@@ -237,10 +240,79 @@ def profiled_traffic(kernel, moves_per_launch):
         return None
 
 
+def run_batch64(args):
+    """64 independent jobs (16 per bcc L in 8, 12, 16, 20; random three-shell couplings; N/4 bins over
+    [E_gs, 0]; 8..32 windows x 4 walkers) in one persistent walker launch per interval, replayed
+    from a CUDA graph after the autotuner picked walkers per block and lattice placement."""
+    import torch
+    import paper_1411_4212_gb300 as rw
+    from paper_1411_4212_gb300 import workloads
+
+    rank, world, local = dist_init(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    I = args.intervals
+    specs = workloads.batch64_jobs()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        jobs = [rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, group_size=1, stream=stream,
+                        **dict(s, seed=s["seed"] + 100000 * rank)) for s in specs]
+        batch = rw.Batch(jobs, stream=stream)
+    setup_s = time.perf_counter() - t0
+    tune = batch.autotune(trial_moves=2000)
+    S = sum(j.n_slots for j in jobs)
+    moves_per_step = S * specs[0]["exchange_interval"] * I
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    batch.run_intervals(max(3, args.warmup))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    clocks.wait_first()
+    barrier(world)
+    step_ms = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.run_intervals(I)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    total_ms = all_max(sum(step_ms), world)
+    value = moves_per_step * args.steps * world / (total_ms * 1e-3)
+    info = batch.info()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32 spins/dE + int64 fixed-point ln g/energy",
+            "data": "synthetic",
+            "config": {"workload": "64 REWL jobs, bcc L in {8,12,16,20} x 16, J1=1 J2~U[0.2,0.6] J3~U[-0.1,0.1], "
+                                   "N/4 bins over [E_gs,0], 8/16/24/32 windows x 4 walkers, exchange every 1e4 moves",
+                       "walker_slots": S, "intervals_per_step": I, "moves_per_step": moves_per_step * world,
+                       "l2": "flushed between steps (256 MB write)", "graph": True,
+                       "tuning": tune, "batch": info, "setup_s": setup_s},
+            "gpu_launches": args.steps * I * 3,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for j in jobs:
+        j.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch64(args)
     import torch
     import paper_1411_4212_gb300 as rw
 

@@ -256,6 +256,71 @@ const char* rewl_last_error(const rewl_handle* h);
 /* Release everything; NULL-safe. */
 void rewl_destroy(rewl_handle* h);
 
+/* ---- Batches: many independent REWL jobs in one persistent walker launch ----------------------
+ * A batch runs the exchange intervals (Sec. 4.2-4.3: Wang-Landau moves, replica exchange,
+ * flatness check and ln f reduction) of many handles at once.  All walker slots of all jobs form
+ * one work list, most expensive first; one persistent launch of the pipelined walker takes slots
+ * from it, `workers_per_block` walker pairs per CTA, each pair with its own shared-memory arena
+ * (a job's lattice sits in the arena or stays in global memory, per the tuning).  One launch each
+ * then does the replica exchange and the flatness check of every job.  The launch sequence of an
+ * interval is captured once into a CUDA graph and replayed.  The paper runs one job per machine;
+ * batching is this library's own addition.  The result of every job is the same as running its
+ * handle alone: in trajectory mode bit for bit, in production mode up to the order of the energy
+ * recomputation's FP64 sum.
+ * Requirements (else REWL_EINVAL): bcc lattices that use the pipelined walker (rewl_info
+ * .pipelined = 1), all in the same mode, with the same number of coupling shells, exchange_interval
+ * and recompute_every.  Walkers not yet initialised are initialised at creation (rewl_init_walkers).
+ * The batch borrows the handles: they must outlive it, and must not be used on other streams
+ * while a batch call runs.  Batch errors are reported by rewl_last_error(NULL). */
+typedef struct rewl_batch rewl_batch; /* opaque, owned by the library */
+
+typedef struct {
+  int workers_per_block;     /* walker pairs (64 threads each) per CTA, 1..3 */
+  int smem_lattice_max_n;    /* jobs with n_spins <= this keep the lattice in shared memory (if it
+                                fits the arena); 0 = none; the others read it from global memory */
+} rewl_batch_tuning;
+
+typedef struct {
+  int n_jobs, n_items;       /* jobs, walker slots over all jobs */
+  int n_active_jobs;         /* jobs in the work list (see rewl_batch_run_to_convergence) */
+  int workers_per_block, smem_lattice_max_n;
+  int grid, blocks_per_sm;   /* persistent launch: CTAs, resident CTAs per SM */
+  int n_smem_lattice_jobs;   /* jobs whose lattice sits in shared memory */
+  int64_t arena_bytes;       /* shared memory per walker pair */
+  int64_t intervals_done;
+  int graphs_built;          /* CUDA graphs instantiated so far */
+} rewl_batch_info;
+
+/* Create a batch over jobs[0..n_jobs-1] (host array of handles) on cuda_stream (NULL: the batch
+ * creates its own non-blocking stream, since a graph cannot be captured on the legacy default
+ * stream).  Work is ordered after each handle's pending work and each handle's stream waits for
+ * the batch's work.  The initial tuning is 2 workers per block, every lattice that fits in shared
+ * memory there. */
+rewl_status rewl_batch_create(rewl_handle* const* jobs, int n_jobs, void* cuda_stream, rewl_batch** out);
+
+/* Set the tuning explicitly (REWL_EINVAL if the tables of some job do not fit). */
+rewl_status rewl_batch_set_tuning(rewl_batch* b, const rewl_batch_tuning* t);
+
+/* Autotuner: time one walker launch of trial_moves moves per walker (> 0) for every candidate
+ * (workers_per_block 1..3 x every lattice-size threshold of the batch's jobs), keep the fastest.
+ * The timed moves are ordinary Wang-Landau moves of the jobs: the walkers advance by them.
+ * chosen (host, may be NULL) receives the tuning; ms_out (host, may be NULL) its trial time. */
+rewl_status rewl_batch_autotune(rewl_batch* b, int64_t trial_moves, rewl_batch_tuning* chosen, double* ms_out);
+
+/* Run n_intervals exchange intervals of every job in the work list (graph replays; the energy
+ * recomputation comes every recompute_every intervals of the batch, as for a handle). */
+rewl_status rewl_batch_run_intervals(rewl_batch* b, int n_intervals);
+
+/* Run intervals until every walker of every job has ln f < ln f_final, checking every
+ * check_every (>= 1) intervals; jobs that finish leave the work list.  Stops after max_intervals
+ * (> 0) with REWL_ETIMEOUT.  n_done (host, may be NULL) receives the number of finished jobs. */
+rewl_status rewl_batch_run_to_convergence(rewl_batch* b, int64_t max_intervals, int check_every, int* n_done);
+
+rewl_status rewl_batch_get_info(const rewl_batch* b, rewl_batch_info* out);
+
+/* Release the batch (not the handles); NULL-safe. */
+void rewl_batch_destroy(rewl_batch* b);
+
 /* Exp as used by the trajectory mode and the exchange acceptance, evaluated on the device for
  * n host inputs (FP64): Cody-Waite reduction and a degree-13 Taylor polynomial.  For tests. */
 rewl_status rewl_device_exp(const double* x, double* y, int n);

@@ -16,7 +16,7 @@ import os
 
 import numpy as np
 
-__all__ = ["REWL", "RewlError", "load_library", "thermo", "stitch_device", "device_exp",
+__all__ = ["REWL", "Batch", "RewlError", "load_library", "thermo", "stitch_device", "device_exp",
            "measure_smem_bandwidth", "BCC", "CHAIN", "TABLE", "PRODUCTION", "TRAJECTORY"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -79,6 +79,20 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class BatchTuning(C.Structure):
+    _fields_ = [("workers_per_block", C.c_int32), ("smem_lattice_max_n", C.c_int32)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_jobs", C.c_int32), ("n_items", C.c_int32), ("n_active_jobs", C.c_int32),
+                ("workers_per_block", C.c_int32), ("smem_lattice_max_n", C.c_int32), ("grid", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("n_smem_lattice_jobs", C.c_int32), ("arena_bytes", C.c_int64),
+                ("intervals_done", C.c_int64), ("graphs_built", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Counters(C.Structure):
     _fields_ = [("moves", C.c_int64), ("accepts", C.c_int64), ("recomputes", C.c_int64)]
 
@@ -127,6 +141,13 @@ def load_library(path=LIB_PATH):
         "rewl_destroy": ([_vp], None),
         "rewl_device_exp": ([_vp, _vp, C.c_int], st),
         "rewl_measure_smem_bandwidth": ([_vp, _vp, _vp], st),
+        "rewl_batch_create": ([C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)], st),
+        "rewl_batch_set_tuning": ([_vp, C.POINTER(BatchTuning)], st),
+        "rewl_batch_autotune": ([_vp, C.c_int64, C.POINTER(BatchTuning), C.POINTER(C.c_double)], st),
+        "rewl_batch_run_intervals": ([_vp, C.c_int], st),
+        "rewl_batch_run_to_convergence": ([_vp, C.c_int64, C.c_int, C.POINTER(C.c_int)], st),
+        "rewl_batch_get_info": ([_vp, C.POINTER(BatchInfo)], st),
+        "rewl_batch_destroy": ([_vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -335,6 +356,62 @@ class REWL:
 
     def centres(self):
         return self.e_min + (np.arange(self.B) + 0.5) * self.dE
+
+
+class Batch:
+    """Many REWL jobs (REWL objects, bcc, same mode / shell count / exchange interval) run together:
+    one persistent walker launch over every walker slot, replayed from a CUDA graph.  The jobs must
+    outlive the batch; their results are read from the REWL objects as usual."""
+
+    def __init__(self, jobs, stream=None):
+        lib = load_library()
+        self._lib = lib
+        self.jobs = list(jobs)
+        arr = (_vp * len(self.jobs))(*[j._h for j in self.jobs])
+        b = _vp()
+        _check(lib.rewl_batch_create(arr, len(self.jobs), _stream_ptr(stream), C.byref(b)))
+        self._b = b
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.rewl_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_tuning(self, workers_per_block, smem_lattice_max_n):
+        t = BatchTuning(int(workers_per_block), int(smem_lattice_max_n))
+        _check(self._lib.rewl_batch_set_tuning(self._b, C.byref(t)))
+
+    def autotune(self, trial_moves=2000):
+        t = BatchTuning()
+        ms = C.c_double()
+        _check(self._lib.rewl_batch_autotune(self._b, int(trial_moves), C.byref(t), C.byref(ms)))
+        return {"workers_per_block": t.workers_per_block, "smem_lattice_max_n": t.smem_lattice_max_n,
+                "trial_ms": ms.value}
+
+    def run_intervals(self, n):
+        _check(self._lib.rewl_batch_run_intervals(self._b, int(n)))
+
+    def run_to_convergence(self, max_intervals, check_every=8):
+        """Returns (converged, n_done_jobs)."""
+        nd = C.c_int()
+        st = self._lib.rewl_batch_run_to_convergence(self._b, int(max_intervals), int(check_every), C.byref(nd))
+        if st not in (OK, ETIMEOUT):
+            _check(st)
+        return st == OK, nd.value
+
+    def info(self):
+        i = BatchInfo()
+        _check(self._lib.rewl_batch_get_info(self._b, C.byref(i)))
+        return i.as_dict()
 
 
 def thermo(lng, centres, n_spins, T, stream=None):

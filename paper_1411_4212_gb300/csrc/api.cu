@@ -11,6 +11,7 @@
 
 #include "../../include/rewl.h"
 #include "device_common.cuh"
+#include "jobs.h"
 #include "walker.h"
 
 using namespace rewl;
@@ -632,6 +633,48 @@ static FlatnessArgs flatness_args(rewl_handle* h) {
   fa.traj = h->traj ? 1 : 0;
   return fa;
 }
+
+}  // extern "C"
+
+// ---- accessors for the batch runner ----
+void rewl::job_view(const rewl_handle* h, JobView* v) {
+  v->kind = h->kind;
+  v->N = h->N;
+  v->z = h->z;
+  v->L = h->L;
+  v->S = h->S;
+  v->W = h->W;
+  v->h = h->h;
+  v->m = h->m;
+  v->n_shells = h->geo.n_shells;
+  v->traj = h->traj;
+  v->pipe = h->pipe;
+  v->initialized = h->initialized;
+  v->broken = h->broken;
+  v->exchange_interval = h->exchange_interval;
+  v->recompute_every = h->recompute_every;
+  v->stream = h->stream;
+}
+
+WalkerArgs rewl::job_walker_args(rewl_handle* h, long long moves, int recompute) {
+  return walker_args(h, false, recompute != 0, moves);
+}
+
+ExchangeArgs rewl::job_exchange_args(rewl_handle* h) {
+  ExchangeArgs ea{};
+  ea.win = windows_of(h);
+  ea.st = state_of(h);
+  ea.ex = h->ex;
+  ea.key1 = h->key1;
+  ea.traj = h->traj ? 1 : 0;
+  return ea;
+}
+
+FlatnessArgs rewl::job_flatness_args(rewl_handle* h) { return flatness_args(h); }
+
+void rewl::job_add_intervals(rewl_handle* h, long long n) { h->intervals_done += n; }
+
+extern "C" {
 
 rewl_status rewl_walk(rewl_handle* h) {
   rewl_status s = check_ready(h);

@@ -1,0 +1,27 @@
+// jobs.h -- what the batch runner (batch.cu) needs to know about a handle (api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/rewl.h"
+#include "walker.h"
+
+namespace rewl {
+
+struct JobView {
+  int kind, N, z, L, S, W, h, m, n_shells;
+  bool traj, pipe, initialized, broken;
+  long long exchange_interval;
+  int recompute_every;
+  cudaStream_t stream;
+};
+
+void job_view(const rewl_handle* h, JobView* v);
+// kernel arguments of one exchange interval of the handle (owner table and lattice placement are
+// set by the caller for the batched walker)
+WalkerArgs job_walker_args(rewl_handle* h, long long moves, int recompute);
+ExchangeArgs job_exchange_args(rewl_handle* h);
+FlatnessArgs job_flatness_args(rewl_handle* h);
+void job_add_intervals(rewl_handle* h, long long n);
+
+}  // namespace rewl

@@ -18,7 +18,7 @@ namespace rewl {
 // the configuration index and the energy; ln g and H stay with the slots.  One CTA, so the round
 // counter is read once and advanced after every pair is done.
 // ------------------------------------------------------------------------------------------------
-__global__ void exchange_kernel(const ExchangeArgs a) {
+__device__ __forceinline__ void exchange_block(const ExchangeArgs& a) {
   __shared__ long long t_s;
   if (threadIdx.x == 0) t_s = *a.st.ex_index;
   __syncthreads();
@@ -85,8 +85,18 @@ __global__ void exchange_kernel(const ExchangeArgs a) {
   if (threadIdx.x == 0) *a.st.ex_index = t + 1;
 }
 
+__global__ void exchange_kernel(const ExchangeArgs a) { exchange_block(a); }
+
+// one CTA per job of a batch
+__global__ void exchange_batch_kernel(const ExchangeArgs* __restrict__ jobs) { exchange_block(jobs[blockIdx.x]); }
+
 cudaError_t launch_exchange(const ExchangeArgs& a, cudaStream_t stream) {
   exchange_kernel<<<1, 256, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exchange_batch(const ExchangeArgs* jobs, int n_jobs, cudaStream_t stream) {
+  exchange_batch_kernel<<<n_jobs, 256, 0, stream>>>(jobs);
   return cudaGetLastError();
 }
 
@@ -95,8 +105,7 @@ cudaError_t launch_exchange(const ExchangeArgs& a, cudaStream_t stream) {
 // the W bins of its window (and sum H > 0); then ln f -> ln f / 2, H -> 0, stage += 1.
 // One warp per walker.
 // ------------------------------------------------------------------------------------------------
-__global__ void flatness_kernel(const FlatnessArgs a) {
-  const int slot = blockIdx.x;
+__device__ __forceinline__ void flatness_warp(const FlatnessArgs& a, const int slot) {
   const int lane = threadIdx.x;
   const int W = a.win.W;
   bool active;
@@ -134,8 +143,46 @@ __global__ void flatness_kernel(const FlatnessArgs a) {
   }
 }
 
+__global__ void flatness_kernel(const FlatnessArgs a) { flatness_warp(a, blockIdx.x); }
+
+// one warp per (job, slot) item of a batch
+__global__ void flatness_batch_kernel(const FlatnessArgs* __restrict__ jobs, const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.x];
+  flatness_warp(jobs[it.x], it.y);
+}
+
+// Walkers still at ln f >= ln f_final, per job: out[i] for job ids[i] (one CTA per job).
+__global__ void count_active_kernel(const FlatnessArgs* __restrict__ jobs, const int* __restrict__ ids, int* out) {
+  const FlatnessArgs& a = jobs[ids[blockIdx.x]];
+  const int S = a.win.h * a.win.m;
+  int n = 0;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const bool active = a.traj ? a.st.lnf[s] >= a.lnf_final : (double)a.st.lnf_fx[s] * kLngUnit >= a.lnf_final;
+    n += active ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(kFullMask, n, o);
+  __shared__ int part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    out[blockIdx.x] = t;
+  }
+}
+
+cudaError_t launch_count_active(const FlatnessArgs* jobs, const int* ids, int n, int* out, cudaStream_t stream) {
+  count_active_kernel<<<n, 128, 0, stream>>>(jobs, ids, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_flatness(const FlatnessArgs& a, int n_slots, cudaStream_t stream) {
   flatness_kernel<<<n_slots, 32, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flatness_batch(const FlatnessArgs* jobs, const int2* items, int n_items, cudaStream_t stream) {
+  flatness_batch_kernel<<<n_items, 32, 0, stream>>>(jobs, items);
   return cudaGetLastError();
 }
 

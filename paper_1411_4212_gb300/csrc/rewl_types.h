@@ -75,6 +75,7 @@ struct WalkerArgs {
   int init;                            // 1: initial drive into the windows
   int recompute;                       // 1: energy recomputation at the end of the launch
   int own_mask;                        // pipelined walker: owner-table size - 1 (power of two)
+  int smem_lattice;                    // batched pipelined walker: 1 = lattice copied into shared memory
   double lnf_final;
 };
 

@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_kernel(const WalkerArgs
     }
   }
   if (a.recompute && !a.init) {
-    const double Ef = full_energy<kTraj>(a, off_s, sx, sy, sz, red);
+    const double Ef = full_energy<kTraj>(a, off_s, sx, sy, sz, red, threadIdx.x, blockDim.x, 0);
     if (tid == 0) {
       if (kTraj) {
         const double d = fabs(Ef - a.st.E[slot]);
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kWalkerThreads) energies_kernel(const WalkerAr
   __syncthreads();
   const int N = a.geo.N;
   const Real* sp = reinterpret_cast<const Real*>(a.st.spins) + (size_t)blockIdx.x * 3 * N;
-  const double e = full_energy<kTraj>(a, off_s, sp, sp + N, sp + 2 * (size_t)N, red);
+  const double e = full_energy<kTraj>(a, off_s, sp, sp + N, sp + 2 * (size_t)N, red, threadIdx.x, blockDim.x, 0);
   if (threadIdx.x == 0) out[blockIdx.x] = e;
 }
 

@@ -18,6 +18,25 @@ size_t walker_pipe_smem_bytes(bool traj, bool smem_lattice, int N, int W, int ow
 cudaError_t launch_walkers_pipe(const WalkerArgs& a, int n_slots, bool traj, bool smem_lattice, size_t smem,
                                 cudaStream_t stream);
 
+// Batched pipelined walker: one persistent launch over (job, slot) items of many jobs with the same
+// mode and shell count.
+constexpr int kBatchMaxWorkers = 3;    // workers (walker pairs) per CTA: barrier ids 1..15
+struct BatchLaunch {
+  const WalkerArgs* jobs;              // device [n_jobs]
+  const int2* items;                   // device [n_items] (job, slot), most expensive first
+  int n_items;
+  int* head;                           // device work-list counter (reset by the launcher)
+  long long moves;                     // trial moves per walker
+  int recompute;                       // energy recomputation at the end of every slot
+  bool traj;
+  int n_shells;
+  int workers;                         // per CTA
+  size_t arena;                        // shared bytes per worker
+  int grid;
+};
+cudaError_t setup_walkers_batch(bool traj, int n_shells, int workers, size_t arena, int* blocks_per_sm);
+cudaError_t launch_walkers_batch(const BatchLaunch& b, cudaStream_t stream);
+
 struct ExchangeArgs {
   Windows win;
   WalkerState st;
@@ -26,6 +45,7 @@ struct ExchangeArgs {
   int traj;
 };
 cudaError_t launch_exchange(const ExchangeArgs& a, cudaStream_t stream);
+cudaError_t launch_exchange_batch(const ExchangeArgs* jobs, int n_jobs, cudaStream_t stream);
 
 struct FlatnessArgs {
   Windows win;
@@ -35,6 +55,9 @@ struct FlatnessArgs {
   int traj;
 };
 cudaError_t launch_flatness(const FlatnessArgs& a, int n_slots, cudaStream_t stream);
+cudaError_t launch_flatness_batch(const FlatnessArgs* jobs, const int2* items, int n_items, cudaStream_t stream);
+// walkers with ln f >= ln f_final of the jobs ids[0..n-1] -> out[0..n-1] (device arrays)
+cudaError_t launch_count_active(const FlatnessArgs* jobs, const int* ids, int n, int* out, cudaStream_t stream);
 
 // Merge: fragments are read from either an FP64 array or a 2^-40 fixed-point array [h][m][W].
 struct MergeArgs {

@@ -204,28 +204,35 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x, float xe) 
   lo += err + xe;
 }
 
-__device__ __forceinline__ double block_sum_double(double v, double* red) {
+// Barrier over the nt threads of a group (id 0 with nt = blockDim.x is __syncthreads()).
+__device__ __forceinline__ void group_sync(int id, int nt) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nt) : "memory");
+}
+
+// Sum over the nt threads t = 0..nt-1 of a group (warp-aligned), valid in thread t = 0.
+__device__ __forceinline__ double block_sum_double(double v, double* red, int t, int nt, int bar) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) red[w] = v;
-  __syncthreads();
+  const int w = t >> 5;
+  if ((t & 31) == 0) red[w] = v;
+  group_sync(bar, nt);
   double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-  __syncthreads();
+  if (t == 0)
+    for (int i = 0; i < (nt >> 5); ++i) s += red[i];
+  group_sync(bar, nt);
   return s;
 }
 
-// Full energy of the CTA's configuration: E = -w sum_i sum_{energy slots} J S_i.S_n.
+// Full energy of a configuration, E = -w sum_i sum_{energy slots} J S_i.S_n, by the nt threads
+// t = 0..nt-1 of a group that synchronises on barrier bar; valid in thread t = 0.
 template <bool kTraj>
 __device__ double full_energy(const WalkerArgs& a, const uint32_t* off_s,
                               const typename Mode<kTraj>::Real* sx, const typename Mode<kTraj>::Real* sy,
-                              const typename Mode<kTraj>::Real* sz, double* red) {
+                              const typename Mode<kTraj>::Real* sz, double* red, int t, int nt, int bar) {
   const int N = a.geo.N;
   const bool bcc = a.geo.kind == 0;
   double part = 0.0;
   float hi = 0.0f, lo = 0.0f;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+  for (int i = t; i < N; i += nt) {
     int X = 0, Y = 0, Z = 0;
     if (bcc) bcc_coords(i, a.geo.L, a.geo.divL, X, Y, Z);
     if (kTraj) {
@@ -284,7 +291,7 @@ __device__ double full_energy(const WalkerArgs& a, const uint32_t* off_s,
     }
   }
   if (!kTraj) part = (double)hi + (double)lo;
-  const double tot = block_sum_double(part, red);
+  const double tot = block_sum_double(part, red, t, nt, bar);
   return -(double)a.geo.energy_weight * tot;
 }
 

@@ -48,10 +48,9 @@ constexpr ShellTable make_shells(int nsh) {
 }
 
 constexpr int kPairThreads = 64;   // resolver warp + producer warp
+constexpr int kWorkerThreads = 64;     // batched walker: threads per worker (one pair)
 
 __host__ __device__ constexpr size_t align16(size_t n) { return (n + 15) & ~(size_t)15; }
-constexpr int kBarReady = 1;       // ids 1, 2
-constexpr int kBarDone = 3;        // ids 3, 4
 
 __device__ __forceinline__ void named_sync(int id) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kPairThreads) : "memory");
@@ -158,15 +157,19 @@ __device__ __forceinline__ int dq24_of(float dE, const Windows& w) {
   return __float2int_rn(p) + __float2int_rn(e);
 }
 
+// One exchange interval of walker slot `slot` by a group of nt threads (tid = 0..nt-1, nt a multiple
+// of 32, at least 64): warp 0 resolves, warp 1 produces, every warp loads and stores.  smem_raw is
+// the group's shared-memory arena (walker_pipe_smem_bytes), red holds nt/32 doubles.  Barrier
+// bar_sync spans the group; bar_pair .. bar_pair+3 are READY(0), READY(1), DONE(0), DONE(1) of the
+// resolver/producer pair.
 template <bool kTraj, bool kSmem, int NSH>
-__global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const WalkerArgs a) {
+__device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int slot, const long long moves,
+                                               const int recompute, unsigned char* smem_raw, double* red,
+                                               const int tid, const int nt, const int bar_sync,
+                                               const int bar_pair) {
   using Real = typename Mode<kTraj>::Real;
   using Lng = typename Mode<kTraj>::Lng;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[kWalkerThreads / 32];
-
-  const int slot = blockIdx.x;
-  const int tid = threadIdx.x;
+  const int kBarReady = bar_pair, kBarDone = bar_pair + 2;
   const int warp = tid >> 5, lane = tid & 31;
   const int N = a.geo.N, W = a.win.W, L = a.geo.L;
   const int wlo = a.win.starts[slot / a.win.m];
@@ -200,23 +203,22 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const Walke
   Real* sz = sx + 2 * (size_t)N;
 
   const size_t lbase = (size_t)slot * W;
-  for (int w = tid; w < W; w += blockDim.x) {
+  for (int w = tid; w < W; w += nt) {
     if constexpr (kTraj)
       lng_s[w] = (Lng)a.st.lng[lbase + w];
     else
       lng_s[w] = (Lng)a.st.lng_fx[lbase + w];
     H_s[w] = a.st.H[lbase + w];
   }
-  for (int j = tid; j < kMaxSlotsPerSite; j += blockDim.x) {
+  for (int j = tid; j < kMaxSlotsPerSite; j += nt) {
     off_s[j] = a.geo.off[j];
     J_s[j] = kTraj ? (Real)a.geo.Jd[j] : (Real)a.geo.Jf[j];
   }
-  for (uint32_t i = tid; i <= omask; i += blockDim.x) own[i] = make_uint2(0u, 0u);
+  for (uint32_t i = tid; i <= omask; i += nt) own[i] = make_uint2(0u, 0u);
   if (kSmem)
-    for (size_t i = tid; i < 3 * (size_t)N; i += blockDim.x) spin_s[i] = gsp[i];
-  __syncthreads();
+    for (size_t i = tid; i < 3 * (size_t)N; i += nt) spin_s[i] = gsp[i];
+  group_sync(bar_sync, nt);
 
-  const long long moves = a.moves;
   const int nb = (int)((moves + 31) / 32);
   const long long t0 = a.st.steps[slot];
   const uint2 key = make_uint2((uint32_t)slot, a.key1);
@@ -667,19 +669,19 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const Walke
     }
    }
   }
-  __syncthreads();
+  group_sync(bar_sync, nt);
 
   if (kSmem)
-    for (size_t i = tid; i < 3 * (size_t)N; i += blockDim.x) gsp[i] = spin_s[i];
-  for (int w = tid; w < W; w += blockDim.x) {
+    for (size_t i = tid; i < 3 * (size_t)N; i += nt) gsp[i] = spin_s[i];
+  for (int w = tid; w < W; w += nt) {
     if constexpr (kTraj)
       a.st.lng[lbase + w] = (double)lng_s[w];
     else
       a.st.lng_fx[lbase + w] = (long long)lng_s[w];
     a.st.H[lbase + w] = H_s[w];
   }
-  if (a.recompute) {
-    const double Ef = full_energy<kTraj>(a, off_s, sx, sy, sz, red);
+  if (recompute) {
+    const double Ef = full_energy<kTraj>(a, off_s, sx, sy, sz, red, tid, nt, bar_sync);
     if (tid == 0) {
       if constexpr (kTraj) {
         const double d = fabs(Ef - a.st.E[slot]);
@@ -697,6 +699,96 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const Walke
       }
     }
   }
+}
+
+template <bool kTraj, bool kSmem, int NSH>
+__global__ void __launch_bounds__(kWalkerThreads) walker_pipe_kernel(const WalkerArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[kWalkerThreads / 32];
+  // one CTA per slot; barrier 0 spans the CTA, 1..4 serve the pair
+  pipe_walk_slot<kTraj, kSmem, NSH>(a, blockIdx.x, a.moves, a.recompute, smem_raw, red, threadIdx.x, blockDim.x, 0,
+                                    1);
+}
+
+// Persistent walker over many jobs: every 64-thread worker (resolver warp + producer warp) takes
+// (job, slot) items from the work list until it is exhausted; a CTA holds `workers` workers, each
+// with its own shared-memory arena and barriers (1 + 5w .. 5 + 5w).  A job's lattice sits in the
+// arena or stays in global memory (L2) as its smem_lattice flag says.
+template <bool kTraj, int NSH>
+__global__ void __launch_bounds__(kBatchMaxWorkers * kWorkerThreads)
+    walker_batch_kernel(const WalkerArgs* __restrict__ jobs, const int2* __restrict__ items, int n_items, int* head,
+                        long long moves, int recompute, unsigned arena) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[kBatchMaxWorkers][kWorkerThreads / 32];
+  __shared__ int next[kBatchMaxWorkers];
+  const int w = threadIdx.x / kWorkerThreads, wt = threadIdx.x % kWorkerThreads;
+  const int bar_sync = 1 + 5 * w, bar_pair = 2 + 5 * w;
+  unsigned char* mine = smem_raw + (size_t)w * arena;
+  for (;;) {
+    // every thread has read next[w] before the first barrier inside the walk, so the next write
+    // cannot overtake a read
+    if (wt == 0) next[w] = atomicAdd(head, 1);
+    group_sync(bar_sync, kWorkerThreads);
+    const int it = next[w];
+    if (it >= n_items) break;
+    const int2 js = items[it];
+    const WalkerArgs& a = jobs[js.x];
+    if (a.smem_lattice)
+      pipe_walk_slot<kTraj, true, NSH>(a, js.y, moves, recompute, mine, red[w], wt, kWorkerThreads, bar_sync,
+                                       bar_pair);
+    else
+      pipe_walk_slot<kTraj, false, NSH>(a, js.y, moves, recompute, mine, red[w], wt, kWorkerThreads, bar_sync,
+                                        bar_pair);
+  }
+}
+
+template <bool kTraj, int NSH>
+static cudaError_t batch_kernel_setup(int workers, size_t arena, int* blocks_per_sm) {
+  const size_t smem = (size_t)workers * arena;
+  cudaError_t e = cudaFuncSetAttribute(walker_batch_kernel<kTraj, NSH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, walker_batch_kernel<kTraj, NSH>,
+                                                       workers * kWorkerThreads, smem);
+}
+
+cudaError_t setup_walkers_batch(bool traj, int n_shells, int workers, size_t arena, int* blocks_per_sm) {
+  if (workers < 1 || workers > kBatchMaxWorkers) return cudaErrorInvalidValue;
+  switch (n_shells * 2 + (traj ? 1 : 0)) {
+    case 2: return batch_kernel_setup<false, 1>(workers, arena, blocks_per_sm);
+    case 3: return batch_kernel_setup<true, 1>(workers, arena, blocks_per_sm);
+    case 4: return batch_kernel_setup<false, 2>(workers, arena, blocks_per_sm);
+    case 5: return batch_kernel_setup<true, 2>(workers, arena, blocks_per_sm);
+    case 6: return batch_kernel_setup<false, 3>(workers, arena, blocks_per_sm);
+    case 7: return batch_kernel_setup<true, 3>(workers, arena, blocks_per_sm);
+    case 8: return batch_kernel_setup<false, 4>(workers, arena, blocks_per_sm);
+    case 9: return batch_kernel_setup<true, 4>(workers, arena, blocks_per_sm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_walkers_batch(const BatchLaunch& b, cudaStream_t stream) {
+  if (b.workers < 1 || b.workers > kBatchMaxWorkers || b.grid < 1) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(b.head, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(b.grid), block(b.workers * kWorkerThreads);
+  const size_t smem = (size_t)b.workers * b.arena;
+  const unsigned arena = (unsigned)b.arena;
+#define REWL_BATCH_LAUNCH(T, S) \
+  walker_batch_kernel<T, S><<<grid, block, smem, stream>>>(b.jobs, b.items, b.n_items, b.head, b.moves, b.recompute, arena)
+  switch (b.n_shells * 2 + (b.traj ? 1 : 0)) {
+    case 2: REWL_BATCH_LAUNCH(false, 1); break;
+    case 3: REWL_BATCH_LAUNCH(true, 1); break;
+    case 4: REWL_BATCH_LAUNCH(false, 2); break;
+    case 5: REWL_BATCH_LAUNCH(true, 2); break;
+    case 6: REWL_BATCH_LAUNCH(false, 3); break;
+    case 7: REWL_BATCH_LAUNCH(true, 3); break;
+    case 8: REWL_BATCH_LAUNCH(false, 4); break;
+    case 9: REWL_BATCH_LAUNCH(true, 4); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef REWL_BATCH_LAUNCH
+  return cudaGetLastError();
 }
 
 size_t walker_pipe_smem_bytes(bool traj, bool smem_lattice, int N, int W, int own_entries) {

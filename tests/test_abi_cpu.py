@@ -62,3 +62,19 @@ def test_no_device_reports_cuda_error():
     with pytest.raises(rw.RewlError) as e:
         rw.REWL(kind=rw.BCC, L=4, J=(1.0, 0.5), n_bins=200, n_windows=4, walkers_per_window=2, stream=0)
     assert e.value.status == rw.ECUDA
+
+
+def test_batch_entry_points_reject_invalid_arguments():
+    import ctypes as C
+    lib = rw.load_library()
+    out = C.c_void_p()
+    assert lib.rewl_batch_create(None, 0, None, C.byref(out)) == rw.EINVAL and not out.value
+    assert b"no jobs" in lib.rewl_last_error(None)
+    arr = (C.c_void_p * 1)(None)
+    assert lib.rewl_batch_create(arr, 1, None, C.byref(out)) == rw.EINVAL
+    assert lib.rewl_batch_create(arr, 1, None, None) == rw.EINVAL
+    assert lib.rewl_batch_get_info(None, None) == rw.EINVAL
+    assert lib.rewl_batch_run_intervals(None, 1) == rw.EINVAL
+    assert lib.rewl_batch_autotune(None, 10, None, None) == rw.EINVAL
+    assert lib.rewl_batch_run_to_convergence(None, 1, 1, None) == rw.EINVAL
+    lib.rewl_batch_destroy(None)

@@ -1,0 +1,139 @@
+"""Batched jobs: many REWL handles in one persistent walker launch replayed from a CUDA graph.
+
+Trajectory mode: every job of a batch must match its own FP64 oracle bit for bit (the batch only
+changes which CTA walks which slot, and in what order), for every tuning: one to three walker pairs
+per CTA, lattices in shared memory, in global memory, or mixed.  Production mode: the batch must
+reproduce each handle run alone bit for bit as long as no energy recomputation intervenes (the
+recomputation's FP64 sum runs over a different number of threads), and run_to_convergence must
+retire every job."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1411_4212_gb300 as rw
+from rewl_pairs import assert_same_state
+
+pytestmark = pytest.mark.gpu
+
+# uneven lattices, window counts, walkers and seeds; two coupling shells throughout
+JOBS = [
+    dict(L=4, J=(1.0, 0.5), n_bins=200, n_windows=4, walkers_per_window=2, seed=1),
+    dict(L=5, J=(1.0, 0.4), n_bins=150, n_windows=3, walkers_per_window=3, seed=2),
+    dict(L=6, J=(1.0, 0.3), n_bins=240, n_windows=5, walkers_per_window=2, seed=3),
+    dict(L=3, J=(1.0, 0.6), n_bins=80, n_windows=2, walkers_per_window=1, seed=4),
+]
+COMMON = dict(overlap=0.75, flatness=0.8, lnf_final=1e-3, exchange_interval=700, group_size=1)
+
+
+def _traj_jobs(specs, recompute_every=0):
+    # the energy recomputation only measures drift in trajectory mode: the oracle needs no cadence
+    gpus = [rw.REWL(kind=rw.BCC, mode=rw.TRAJECTORY, recompute_every=recompute_every, **s, **COMMON)
+            for s in specs]
+    orcs = [oracle.OracleREWL(kind=oracle.BCC, init_max_moves=1 << 40, **s, **COMMON) for s in specs]
+    for g in gpus:
+        assert g.info()["pipelined"] == 1
+    return gpus, orcs
+
+
+@pytest.mark.parametrize("workers,smem_max_n", [(1, 0), (2, 300), (3, 1 << 30)])
+def test_batch_trajectory_matches_oracle(workers, smem_max_n):
+    gpus, orcs = _traj_jobs(JOBS)
+    for o in orcs:
+        o.init_walkers()
+    with rw.Batch(gpus) as b:
+        b.set_tuning(workers, smem_max_n)
+        info = b.info()
+        assert info["workers_per_block"] == workers and info["n_items"] == sum(g.n_slots for g in gpus)
+        n_smem = sum(1 for g in gpus if g.N <= smem_max_n)
+        assert info["n_smem_lattice_jobs"] == n_smem
+        b.run_intervals(5)
+        assert b.info()["graphs_built"] >= 1
+    for o in orcs:
+        o.run_intervals(5)
+    for g, o in zip(gpus, orcs):
+        assert_same_state(g, o)
+        lg, _ = g.merge()
+        lo, _ = o.merge()
+        assert np.array_equal(lg.view(np.int64), lo.view(np.int64))
+        g.close()
+
+
+def test_batch_trajectory_graph_cadence_with_recompute_every():
+    """recompute_every = 3: the R-interval graph and the single-interval graphs interleave."""
+    gpus, orcs = _traj_jobs(JOBS[:2], recompute_every=3)
+    for o in orcs:
+        o.init_walkers()
+    with rw.Batch(gpus) as b:
+        for n in (1, 4, 2, 3):
+            b.run_intervals(n)
+        assert b.info()["intervals_done"] == 10
+    for o in orcs:
+        o.run_intervals(10)
+    for g, o in zip(gpus, orcs):
+        assert_same_state(g, o)
+        g.close()
+
+
+def test_batch_production_equals_single_runs_before_recompute():
+    specs = [dict(s) for s in JOBS[:3]]
+    mk = lambda s: rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, recompute_every=1000, **s, **COMMON)
+    singles = [mk(s) for s in specs]
+    batched = [mk(s) for s in specs]
+    for g in singles:
+        g.init_walkers()
+        g.run_intervals(4, stats=False)
+    with rw.Batch(batched) as b:
+        b.set_tuning(2, 300)
+        b.run_intervals(4)
+    for g1, g2 in zip(singles, batched):
+        w1, w2 = g1.walkers(), g2.walkers()
+        for k in ("H", "bin", "replica", "accepts", "steps", "stage"):
+            assert np.array_equal(w1[k], w2[k]), k
+        for k in ("lng", "E", "lnf"):
+            assert np.array_equal(w1[k].view(np.int64), w2[k].view(np.int64)), k
+        assert np.array_equal(g1.spins().view(np.int64), g2.spins().view(np.int64))
+        g1.close()
+        g2.close()
+
+
+def test_batch_autotune_and_convergence():
+    """Restricted energy range (bins narrower than the temperature there): converges in seconds."""
+    jobs = [rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, L=4, J=(1.0, j2), e_min=-400.0, e_max=0.0, n_bins=120,
+                    n_windows=3, walkers_per_window=2, overlap=0.75, flatness=0.8, lnf_final=1e-4, seed=s,
+                    exchange_interval=2000, group_size=1)
+            for s, j2 in enumerate((0.3, 0.45, 0.6), start=11)]
+    with rw.Batch(jobs) as b:
+        steps0 = [j.walkers()["steps"].copy() for j in jobs]
+        t = b.autotune(trial_moves=500)
+        assert 1 <= t["workers_per_block"] <= 3 and t["trial_ms"] > 0
+        info = b.info()
+        assert info["workers_per_block"] == t["workers_per_block"]
+        # the timed trials are ordinary moves: every walker advanced by the same count
+        adv = [j.walkers()["steps"] - s0 for j, s0 in zip(jobs, steps0)]
+        assert len({int(a.min()) for a in adv} | {int(a.max()) for a in adv}) == 1
+        converged, n_done = b.run_to_convergence(max_intervals=20000, check_every=16)
+        assert converged and n_done == len(jobs)
+        assert b.info()["n_active_jobs"] == 0
+    for j in jobs:
+        w = j.walkers()
+        assert np.all(w["lnf"] < 1e-4)
+        lng, _ = j.merge()
+        assert np.all(np.isfinite(lng))
+        j.close()
+
+
+def test_batch_rejects_mixed_jobs():
+    a = rw.REWL(kind=rw.BCC, mode=rw.TRAJECTORY, **JOBS[0], **COMMON)
+    b = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, **JOBS[1], **COMMON)
+    c = rw.REWL(kind=rw.BCC, mode=rw.TRAJECTORY, L=4, J=(1.0, 0.5, 0.1), n_bins=100, n_windows=2,
+                walkers_per_window=1, seed=5, **COMMON)
+    for pair in ((a, b), (a, c), (a, a)):
+        with pytest.raises(rw.RewlError) as e:
+            rw.Batch(list(pair))
+        assert e.value.status == rw.EINVAL
+    with rw.Batch([a]) as bt:
+        with pytest.raises(rw.RewlError):
+            bt.set_tuning(4, 0)
+        assert bt.info()["workers_per_block"] == 2   # the previous tuning stays
+    for h in (a, b, c):
+        h.close()
