@@ -47,9 +47,9 @@ def parse():
     p.add_argument("--intervals", type=int, default=20, help="exchange intervals per step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--workload", default="single", choices=["single", "batch64"],
+    p.add_argument("--workload", default="single", choices=["single", "batch64", "warmstart"],
                    help="single: one job, bcc L=16 (the headline line); batch64: 64 jobs of bcc L=8..20 "
-                        "in one persistent launch")
+                        "in one persistent launch; warmstart: learned warm start versus plain REWL")
     return p.parse_args()
 
 
@@ -307,12 +307,56 @@ def run_batch64(args):
     return 0
 
 
+def run_warmstart(args):
+    """Time to converged ln g with and without the learned warm start.  Corpus: 192 converged REWL
+    runs (bcc L = 4, 5, 6 x 64 random three-shell coupling sets, ln f -> 1e-4) on the restricted
+    range [0.6 E_gs, 0] with one bin per spin; the network is trained on them by the library's
+    kernels; evaluation: 4 held-out coupling sets at bcc L = 8 (1024 spins, 16 windows x 2 walkers,
+    ln f -> 1e-5), 2 cold and 2 warm replicas each, cold and warm converged in separate timed batches."""
+    import numpy as np
+    import torch
+    from paper_1411_4212_gb300 import warmstart, workloads
+    rank, world, local = dist_init(args.gpus)
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    x, t, off, meta = warmstart.corpus(sizes=(4, 5, 6), per_size=64, lnf_final=1e-4)
+    t1 = time.perf_counter()
+    net, hist = warmstart.train(x, t, off, steps=4000, lr=2e-3)
+    t2 = time.perf_counter()
+    held = [workloads.random_couplings(20_000 + i) for i in range(4)]
+    ok, res, wall = warmstart.warm_vs_cold(net, 8, held, lnf_final=1e-5, replicas=2, separate=True)
+    cold = float(np.mean([m for r in res for m in r["cold_moves"]]))
+    warm = float(np.mean([m for r in res for m in r["warm_moves"]]))
+    line = {
+        "metric": "time to converged ln g, warm start / plain", "value": wall[1] / wall[0], "unit": "ratio",
+        "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": "warm start: corpus 192 runs bcc L=4,5,6 (ln f->1e-4), evaluation 4 held-out "
+                               "coupling sets at bcc L=8, 16 windows x 2 walkers, ln f->1e-5, range [0.6 E_gs, 0], "
+                               "one bin per spin, ln f0 = 2^-7 (warm) vs 1 (plain)",
+                   "converged": bool(ok and meta["converged"])},
+        "wall_s": {"plain": wall[0], "warm": wall[1], "corpus": t1 - t0, "training": t2 - t1},
+        "moves_per_walker": {"plain": cold, "warm": warm, "ratio": warm / cold},
+        "rms": {"prediction": float(np.mean([r["prediction_rms"] for r in res])),
+                "plain_vs_plain": float(np.mean([v for r in res for v in r["cold_rms"]])),
+                "warm_vs_plain": float(np.mean([v for r in res for v in r["warm_rms"]]))},
+        "training": {"samples": int(len(t)), "runs": int(len(off) - 1), "steps": 4000,
+                     "loss_first": float(hist[0]), "loss_last": float(hist[-1])},
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch64(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     import torch
     import paper_1411_4212_gb300 as rw
 

@@ -321,6 +321,65 @@ rewl_status rewl_batch_get_info(const rewl_batch* b, rewl_batch_info* out);
 /* Release the batch (not the handles); NULL-safe. */
 void rewl_batch_destroy(rewl_batch* b);
 
+/* ---- Learned warm start: an MLP from (E/N, 1/L, J1..J4) to ln g(E)/N ---------------------------
+ * The paper has no learned part; this is the library's own addition.  The network is trained on
+ * ln g curves that REWL runs of this library produced (over random coupling sets).  It gives every
+ * walker an initial ln g; plain Wang-Landau then runs every stage from a small ln f0, so the
+ * network can only save ln f reductions and never decides the result.
+ * Architecture (fixed): 6 inputs x = (E/N, 1/L, J1, J2, J3, J4) (J of shells past the last = 0),
+ * each shifted and scaled, x' = (x - in_shift) * in_scale; 3 hidden layers of 128 SiLU units; one
+ * linear output y ~ ln g/N.  Weights and biases are used in BF16, rounded from an FP32 master copy;
+ * activations and accumulations are FP32.  Parameters (REWL_MLP_PARAMS FP32 values, transposed
+ * weights WT[k][j] = weight from input k to unit j):
+ *   WT1 [6][128] | b1 [128] | WT2 [128][128] | b2 [128] | WT3 [128][128] | b3 [128] | WT4 [128] | b4.
+ * Loss over a corpus of runs g with samples seg[g] .. seg[g+1]-1 (ln g is defined up to a constant
+ * per run): L = (1/M) sum_g sum_s (r_s - mean_g r)^2, r = y - target, M = all samples.
+ * Errors are reported by rewl_last_error(NULL). */
+typedef struct rewl_mlp rewl_mlp; /* opaque, owned by the library */
+#define REWL_MLP_INPUTS 6
+#define REWL_MLP_PARAMS 34049
+
+/* Number of FP32 parameters (REWL_MLP_PARAMS). */
+int64_t rewl_mlp_param_count(void);
+
+/* in_shift, in_scale: host [6] (finite, scales nonzero).  Initial weights uniform in
+ * +-1/sqrt(fan_in) from a generator seeded by seed, biases 0.  Work runs on cuda_stream. */
+rewl_status rewl_mlp_create(const float* in_shift, const float* in_scale, uint64_t seed, void* cuda_stream,
+                            rewl_mlp** out);
+
+/* Replace the FP32 master parameters (host [REWL_MLP_PARAMS]); the BF16 copy follows and the Adam
+ * state is cleared. */
+rewl_status rewl_mlp_set_params(rewl_mlp* m, const float* params);
+
+/* Host copies of the FP32 master (params, may be NULL) and of the BF16 weights the kernels use
+ * (params_bf16, raw bfloat16 bit patterns, may be NULL). */
+rewl_status rewl_mlp_get_params(rewl_mlp* m, float* params, uint16_t* params_bf16);
+
+/* Inference: x host [n][6] raw inputs, y host [n]. */
+rewl_status rewl_mlp_forward(rewl_mlp* m, const float* x, int64_t n, float* y);
+
+/* Full-batch loss and gradient: x [M][6], target [M], run_offsets [n_runs + 1] (0 = first, M =
+ * last, increasing); loss (host, may be NULL) and grad (host [REWL_MLP_PARAMS], may be NULL).  The
+ * gradient is summed in a fixed order (deterministic). */
+rewl_status rewl_mlp_gradient(rewl_mlp* m, const float* x, const float* target, const int32_t* run_offsets,
+                              int n_runs, double* loss, float* grad);
+
+/* steps (>= 1) full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr > 0) on the
+ * device; loss_history (host [steps], may be NULL) receives the loss before each step. */
+rewl_status rewl_mlp_train(rewl_mlp* m, const float* x, const float* target, const int32_t* run_offsets,
+                           int n_runs, int steps, float lr, float* loss_history);
+
+/* Inputs of the handle's bins (bcc): x_out host [n_bins][6] at the bin centres; with lng (host
+ * [n_bins], e.g. from rewl_merge_lng) t_out (host [n_bins], may be NULL) receives ln g/N. */
+rewl_status rewl_mlp_features(const rewl_handle* h, const double* lng, float* x_out, float* t_out);
+
+/* Warm start: predict ln g = N y at the handle's bins and install it in every walker with ln f =
+ * lnf0 (> 0) (rewl_set_initial_lng).  lng_out (host [n_bins], may be NULL) receives the prediction. */
+rewl_status rewl_mlp_warm_start(rewl_mlp* m, rewl_handle* h, double lnf0, double* lng_out);
+
+/* Release the model; NULL-safe. */
+void rewl_mlp_destroy(rewl_mlp* m);
+
 /* Exp as used by the trajectory mode and the exchange acceptance, evaluated on the device for
  * n host inputs (FP64): Cody-Waite reduction and a degree-13 Taylor polynomial.  For tests. */
 rewl_status rewl_device_exp(const double* x, double* y, int n);

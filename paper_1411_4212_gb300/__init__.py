@@ -16,7 +16,7 @@ import os
 
 import numpy as np
 
-__all__ = ["REWL", "Batch", "RewlError", "load_library", "thermo", "stitch_device", "device_exp",
+__all__ = ["REWL", "Batch", "Mlp", "RewlError", "load_library", "thermo", "stitch_device", "device_exp",
            "measure_smem_bandwidth", "BCC", "CHAIN", "TABLE", "PRODUCTION", "TRAJECTORY"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -148,6 +148,16 @@ def load_library(path=LIB_PATH):
         "rewl_batch_run_to_convergence": ([_vp, C.c_int64, C.c_int, C.POINTER(C.c_int)], st),
         "rewl_batch_get_info": ([_vp, C.POINTER(BatchInfo)], st),
         "rewl_batch_destroy": ([_vp], None),
+        "rewl_mlp_param_count": ([], C.c_int64),
+        "rewl_mlp_create": ([_vp, _vp, C.c_uint64, _vp, C.POINTER(_vp)], st),
+        "rewl_mlp_set_params": ([_vp, _vp], st),
+        "rewl_mlp_get_params": ([_vp, _vp, _vp], st),
+        "rewl_mlp_forward": ([_vp, _vp, C.c_int64, _vp], st),
+        "rewl_mlp_gradient": ([_vp, _vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), _vp], st),
+        "rewl_mlp_train": ([_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp], st),
+        "rewl_mlp_features": ([_vp, _vp, _vp, _vp], st),
+        "rewl_mlp_warm_start": ([_vp, _vp, C.c_double, _vp], st),
+        "rewl_mlp_destroy": ([_vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -412,6 +422,92 @@ class Batch:
         i = BatchInfo()
         _check(self._lib.rewl_batch_get_info(self._b, C.byref(i)))
         return i.as_dict()
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+class Mlp:
+    """Learned warm start: MLP (E/N, 1/L, J1..J4) -> ln g/N, trained and evaluated by the library's
+    kernels.  shift/scale: the fixed input normalisation x' = (x - shift) * scale (6 values each)."""
+
+    N_IN = 6
+
+    def __init__(self, shift, scale, seed=0, stream=None):
+        lib = load_library()
+        self._lib = lib
+        self.n_params = int(lib.rewl_mlp_param_count())
+        sh, sc = _f32(shift), _f32(scale)
+        m = _vp()
+        _check(lib.rewl_mlp_create(_ptr(sh), _ptr(sc), int(seed), _stream_ptr(stream), C.byref(m)))
+        self._m = m
+
+    def close(self):
+        if getattr(self, "_m", None):
+            self._lib.rewl_mlp_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        self.close()
+
+    def set_params(self, p):
+        p = _f32(p)
+        assert p.size == self.n_params
+        _check(self._lib.rewl_mlp_set_params(self._m, _ptr(p)))
+
+    def params(self, bf16=False):
+        """FP32 master parameters, or (bf16=True) the BF16 weights the kernels use, widened to FP32."""
+        if bf16:
+            raw = np.zeros(self.n_params, dtype=np.uint16)
+            _check(self._lib.rewl_mlp_get_params(self._m, None, _ptr(raw)))
+            return (raw.astype(np.uint32) << 16).view(np.float32)
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _check(self._lib.rewl_mlp_get_params(self._m, _ptr(p), None))
+        return p
+
+    def forward(self, x):
+        x = _f32(x, (-1, self.N_IN))
+        y = np.zeros(x.shape[0], dtype=np.float32)
+        _check(self._lib.rewl_mlp_forward(self._m, _ptr(x), x.shape[0], _ptr(y)))
+        return y
+
+    def gradient(self, x, target, run_offsets):
+        x = _f32(x, (-1, self.N_IN))
+        t = _f32(target)
+        seg = np.ascontiguousarray(run_offsets, dtype=np.int32)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = C.c_double()
+        _check(self._lib.rewl_mlp_gradient(self._m, _ptr(x), _ptr(t), _ptr(seg), seg.size - 1, C.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def train(self, x, target, run_offsets, steps, lr):
+        x = _f32(x, (-1, self.N_IN))
+        t = _f32(target)
+        seg = np.ascontiguousarray(run_offsets, dtype=np.int32)
+        hist = np.zeros(int(steps), dtype=np.float32)
+        _check(self._lib.rewl_mlp_train(self._m, _ptr(x), _ptr(t), _ptr(seg), seg.size - 1, int(steps), float(lr),
+                                        _ptr(hist)))
+        return hist
+
+    def warm_start(self, job, lnf0):
+        """Install the predicted ln g in every walker of `job` (a REWL) with ln f = lnf0."""
+        lng = np.zeros(job.B)
+        _check(self._lib.rewl_mlp_warm_start(self._m, job._h, float(lnf0), _ptr(lng)))
+        return lng
+
+
+def mlp_features(job, lng=None):
+    """(x [n_bins][6], ln g/N [n_bins] or None) of a bcc REWL job's bins."""
+    lib = load_library()
+    x = np.zeros((job.B, Mlp.N_IN), dtype=np.float32)
+    t = np.zeros(job.B, dtype=np.float32) if lng is not None else None
+    lp = None if lng is None else np.ascontiguousarray(lng, dtype=np.float64)
+    _check(lib.rewl_mlp_features(job._h, _ptr(lp), _ptr(x), _ptr(t)))
+    return x, t
 
 
 def thermo(lng, centres, n_spins, T, stream=None):

@@ -674,6 +674,14 @@ FlatnessArgs rewl::job_flatness_args(rewl_handle* h) { return flatness_args(h); 
 
 void rewl::job_add_intervals(rewl_handle* h, long long n) { h->intervals_done += n; }
 
+void rewl::job_couplings(const rewl_handle* h, double J[4], double* e_min, double* dE) {
+  for (int s = 0; s < 4; ++s) J[s] = s < h->geo.n_shells ? h->geo.Jsh_d[s] : 0.0;
+  *e_min = h->e_min;
+  *dE = h->dE;
+}
+
+int rewl::job_bins(const rewl_handle* h) { return h->B; }
+
 extern "C" {
 
 rewl_status rewl_walk(rewl_handle* h) {

@@ -23,5 +23,8 @@ WalkerArgs job_walker_args(rewl_handle* h, long long moves, int recompute);
 ExchangeArgs job_exchange_args(rewl_handle* h);
 FlatnessArgs job_flatness_args(rewl_handle* h);
 void job_add_intervals(rewl_handle* h, long long n);
+// coupling per shell (0 past the last shell), energy range start and bin width, number of bins
+void job_couplings(const rewl_handle* h, double J[4], double* e_min, double* dE);
+int job_bins(const rewl_handle* h);
 
 }  // namespace rewl

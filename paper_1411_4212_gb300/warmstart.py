@@ -1,0 +1,135 @@
+"""Learned warm start, end to end, on the library's public API: REWL runs that converge produce
+ln g curves over random coupling sets; the MLP is trained on them by the library's kernels; a
+held-out job starts from the predicted ln g at a small ln f0 and plain Wang-Landau finishes it.
+This module only sequences library calls (every sampling, training and inference step runs on
+the GPU); the numbers it compares are the jobs' own outputs.
+
+Runs use a restricted energy range [0.6 E_gs, 0] with one bin per spin, so that the bin width stays
+near the microcanonical temperature at the lower edge and every run converges in seconds (over
+[E_gs, 0] with N/4 bins the lowest window does not converge at any speed: the bins there are far
+wider than the temperature).
+"""
+import numpy as np
+
+from . import REWL, Batch, Mlp, BCC, PRODUCTION, mlp_features
+from . import workloads
+
+WINDOWS = {4: 4, 5: 6, 6: 8, 7: 12, 8: 16}
+# input normalisation x' = (x - SHIFT) * SCALE of (E/N, 1/L, J1, J2, J3, J4)
+SHIFT = np.array([-1.9, 0.19, 1.0, 0.4, 0.0, 0.0], dtype=np.float32)
+SCALE = np.array([1 / 1.1, 20.0, 1.0, 5.0, 10.0, 1.0], dtype=np.float32)
+LNF0_WARM = 2.0 ** -7
+
+
+def ground_state(L, J):
+    """E_gs of the couplings (Luttinger-Tisza, computed by the library at creation)."""
+    p = REWL(kind=BCC, L=L, J=J, n_bins=16, n_windows=1, walkers_per_window=1, group_size=1)
+    e = p.info()["e_min"]
+    p.close()
+    return e
+
+
+def restricted_job(L, J, seed, lnf_final, walkers=2, exchange_interval=4000, stream=None):
+    N = 2 * L ** 3
+    return REWL(kind=BCC, mode=PRODUCTION, L=L, J=J, e_min=0.6 * ground_state(L, J), e_max=0.0, n_bins=N,
+                n_windows=WINDOWS[L], walkers_per_window=walkers, overlap=0.75, flatness=0.8, lnf_final=lnf_final,
+                seed=seed, exchange_interval=exchange_interval, group_size=1, stream=stream)
+
+
+def converge(jobs, max_intervals=400000, check_every=8, autotune=True):
+    """Run jobs together until all converge; returns True if they did."""
+    with Batch(jobs) as b:
+        if autotune and len(jobs) > 1:
+            b.autotune(trial_moves=200)
+        ok, _ = b.run_to_convergence(max_intervals=max_intervals, check_every=check_every)
+    return ok
+
+
+def corpus(sizes=(4, 5, 6), per_size=64, lnf_final=1e-4, seed0=0):
+    """Converged ln g curves over random couplings: (x [M][6], ln g/N [M], run offsets [R+1], meta)."""
+    jobs, meta = [], []
+    k = seed0
+    for L in sizes:
+        for _ in range(per_size):
+            J = workloads.random_couplings(k)
+            jobs.append(restricted_job(L, J, seed=5000 + k, lnf_final=lnf_final))
+            meta.append((L, J))
+            k += 1
+    ok = converge(jobs)
+    xs, ts = [], []
+    for j in jobs:
+        lng, _ = j.merge()
+        x, t = mlp_features(j, lng)
+        xs.append(x)
+        ts.append(t)
+        j.close()
+    off = np.cumsum([0] + [len(t) for t in ts]).astype(np.int32)
+    return np.concatenate(xs), np.concatenate(ts), off, dict(converged=ok, runs=meta)
+
+
+def train(x, t, off, steps=2000, lr=2e-3, seed=0, stream=None):
+    net = Mlp(SHIFT, SCALE, seed=seed, stream=stream)
+    hist = net.train(x, t, off, steps=steps, lr=lr)
+    return net, hist
+
+
+def centred_rms(a, b):
+    d = np.asarray(a) - np.asarray(b)
+    return float(np.sqrt(np.mean((d - d.mean()) ** 2)))
+
+
+def warm_vs_cold(net, L, couplings, lnf_final=1e-5, replicas=2, lnf0=LNF0_WARM, seed0=900, separate=False):
+    """For every coupling set: `replicas` cold starts (ln g = 0, ln f0 = 1) and `replicas` warm starts
+    (network ln g, ln f0).  Returns (converged, per-set records, wall seconds).  Records hold the moves
+    per walker to converge and the centred rms of each converged ln g against the first cold
+    replica; a job's walkers all walk until the whole job has converged, so its moves per walker are
+    the job's time to converge.  separate=False converges all jobs in one batch (wall = None);
+    separate=True converges the cold jobs, then the warm jobs (network inference included), in two
+    timed batches: wall = (cold seconds, warm seconds)."""
+    import time
+    cold, warm, pred = [], [], []
+    s = seed0
+    for J in couplings:
+        cold.append([restricted_job(L, J, seed=s + r, lnf_final=lnf_final) for r in range(replicas)])
+        warm.append([restricted_job(L, J, seed=s + 100 + r, lnf_final=lnf_final) for r in range(replicas)])
+        s += 1000
+    for group in cold + warm:
+        for j in group:
+            j.init_walkers()
+
+    def start_warm():
+        for ws in warm:
+            for w in ws:
+                p = net.warm_start(w, lnf0)
+            pred.append(p)
+
+    flat_cold = [j for group in cold for j in group]
+    flat_warm = [j for group in warm for j in group]
+    if separate:
+        t0 = time.perf_counter()
+        ok = converge(flat_cold, autotune=False)
+        t1 = time.perf_counter()
+        start_warm()
+        ok = converge(flat_warm, autotune=False) and ok
+        t2 = time.perf_counter()
+        wall = (t1 - t0, t2 - t1)
+    else:
+        start_warm()
+        ok = converge(flat_cold + flat_warm, autotune=False)
+        wall = None
+    out = []
+    for J, cs, ws, p in zip(couplings, cold, warm, pred):
+        ref, _ = cs[0].merge()
+        rec = dict(J=J, cold_moves=[], warm_moves=[], cold_rms=[], warm_rms=[],
+                   prediction_rms=centred_rms(p, ref))
+        for j in cs:
+            rec["cold_moves"].append(float(j.walkers()["steps"].mean()))
+        for j in cs[1:]:
+            rec["cold_rms"].append(centred_rms(j.merge()[0], ref))
+        for j in ws:
+            rec["warm_moves"].append(float(j.walkers()["steps"].mean()))
+            rec["warm_rms"].append(centred_rms(j.merge()[0], ref))
+        out.append(rec)
+        for j in cs + ws:
+            j.close()
+    return ok, out, wall
