@@ -68,9 +68,11 @@ struct alignas(16) Rec<false> {
   uint32_t cprev;        // batch b-1 moves touching this move's neighbourhood
   uint32_t ccur;         // earlier moves of this batch touching it
   int site;
-  float nx, ny;
-  float nz;
-  int pad[3];
+  float nx, ny, nz;      // proposed spin
+  float ox, oy, oz;      // spin at the site before the move (snapshot, corrected by the resolver)
+  float hx, hy, hz;      // local field (snapshot, corrected by the resolver)
+  float dsx, dsy, dsz;   // new - old spin: the move's change to the lattice if accepted
+  int pad[2];
 };
 template <>
 struct alignas(16) Rec<true> {
@@ -282,6 +284,15 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         const float dE = -fmaf(dz, hz, fmaf(dy, hy, dx * hx));
         r.dq = (long long)dq24_of(dE, a.win) << 8;
         r.lu = lu;
+        r.ox = ox;
+        r.oy = oy;
+        r.oz = oz;
+        r.hx = hx;
+        r.hy = hy;
+        r.hz = hz;
+        r.dsx = dx;
+        r.dsy = dy;
+        r.dsz = dz;
       }
       r.cprev = b > 0 ? oprev : 0u;
       r.ccur = ocur & ((1u << lane) - 1u);
@@ -471,8 +482,15 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
     }
    } else {
     // ------------------------ resolver (production mode) ------------------------
-    // Current bin: its ln g and H live in registers (lng_now, h_now) and are written back only
-    // when the walker leaves the bin; ln g of the two neighbouring bins is cached (lng_m, lng_p).
+    // The lattice holds every batch up to b-2 while batch b is resolved: batch b-1's accepted spins
+    // are written at the start of batch b, after the producer has read the lattice for batch b.  A
+    // move's energy change then follows exactly from the producer's snapshot (field h, old spin o)
+    // and the accepted moves of batch b-1 and of batch b before it that touch its neighbourhood:
+    // each adds J (S' - S) to h, or replaces o when it sits on the move's own site.  Corrections
+    // from batch b-1 are applied by every lane at the start of the batch; those from batch b are
+    // out-of-line events of the sequential part.
+    // Current bin: its ln g and H stay in registers and are written back only when the walker
+    // leaves the bin; ln g of the two neighbouring bins is cached (lng_m, lng_p).
     long long Efx = a.st.efx[slot];
     int bcur = fx_bin(Efx);
     float Jsh_r[4];
@@ -491,6 +509,55 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       lng_m = bcur - 1 >= wlo ? (long long)lng_s[bcur - 1 - wlo] : 0;
       lng_p = bcur + 1 < wlo + W ? (long long)lng_s[bcur + 1 - wlo] : 0;
     }
+    // coupling between sites p and q: J of q's shell around p, 0 if q is not a neighbour (every
+    // offset component is below L half-units, so the wrapped displacement is the offset itself)
+    auto coupling = [&](int p, int q) -> float {
+      int Xp, Yp, Zp, Xq, Yq, Zq;
+      bcc_coords(p, L, a.geo.divL, Xp, Yp, Zp);
+      bcc_coords(q, L, a.geo.divL, Xq, Yq, Zq);
+      int dx = Xq - Xp, dy = Yq - Yp, dz = Zq - Zp;
+      dx += dx < -L ? 2 * L : 0;
+      dx -= dx >= L ? 2 * L : 0;
+      dy += dy < -L ? 2 * L : 0;
+      dy -= dy >= L ? 2 * L : 0;
+      dz += dz < -L ? 2 * L : 0;
+      dz -= dz >= L ? 2 * L : 0;
+      const int r2 = dx * dx + dy * dy + dz * dz;
+      const int sh = r2 == 3 ? 0 : (r2 == 4 ? 1 : (r2 == 8 ? 2 : (r2 == 11 ? 3 : 4)));
+      return sh < NSH ? Jsh_r[sh] : 0.0f;
+    };
+    // field and old spin of a move at site p after the accepted moves m of record block R, in order
+    auto correct = [&](const Rec<false>* R, uint32_t m, int p, float& hx, float& hy, float& hz, float& ox, float& oy,
+                       float& oz) {
+      while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1u;
+        const Rec<false>& rj = R[j];
+        const int q = rj.site;
+        if (q == p) {
+          ox = rj.nx;
+          oy = rj.ny;
+          oz = rj.nz;
+        } else {
+          const float J = coupling(p, q);
+          hx = fmaf(J, rj.dsx, hx);
+          hy = fmaf(J, rj.dsy, hy);
+          hz = fmaf(J, rj.dsz, hz);
+        }
+      }
+    };
+    // write the accepted spins of record block R (the last accepted move per site)
+    auto publish = [&](const Rec<false>* R, uint32_t acc) {
+      const Rec<false>& rp = R[lane];
+      const bool mine_acc = (acc >> lane) & 1u;
+      const uint32_t same = __match_any_sync(kFullMask, mine_acc ? rp.site : -1 - lane);
+      if (mine_acc && (same >> lane) == 1u) {
+        sx[rp.site] = rp.nx;
+        sy[rp.site] = rp.ny;
+        sz[rp.site] = rp.nz;
+      }
+      __syncwarp();
+    };
     // segment state: the walker entered bcur (or the batch began) at move k_seg with ln g = lng_seg
     // and histogram h_seg; after j more moves there, ln g = lng_seg + j ln f
     long long lng_seg = lng_in;
@@ -503,11 +570,44 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       named_sync(kBarReady + cur);
       const int nvalid = bad ? 0 : (int)(moves - (long long)b * 32 < 32 ? moves - (long long)b * 32 : 32);
       int k_seg = 0;
-      uint32_t acc_cur = 0, stored = 0;
+      uint32_t acc_cur = 0;
+      Rec<false>* Rc = rec + cur * 32;
+      const Rec<false>* Rp = rec + (cur ^ 1) * 32;
       // ---- parallel part: lane = move index ----
-      const Rec<false>& mine = rec[cur * 32 + lane];
+      Rec<false>& mine = Rc[lane];
       const int my_lu = mine.lu;
-      const uint32_t need_prev = __ballot_sync(kFullMask, lane < nvalid && (mine.cprev & acc_prev) != 0u);
+      {
+        // accepted moves of batch b-1 around this move: correct h and o, then dE
+        const uint32_t m = lane < nvalid ? (mine.cprev & acc_prev) : 0u;
+        if (m) {
+          float hx = mine.hx, hy = mine.hy, hz = mine.hz, ox = mine.ox, oy = mine.oy, oz = mine.oz;
+          correct(Rp, m, mine.site, hx, hy, hz, ox, oy, oz);
+          const float dx = mine.nx - ox, dy = mine.ny - oy, dz = mine.nz - oz;
+          const float dE = -fmaf(dz, hz, fmaf(dy, hy, dx * hx));
+          const long long dq = (long long)dq24_of(dE, a.win) << 8;
+          mine.dq = dq;
+          mine.hx = hx;
+          mine.hy = hy;
+          mine.hz = hz;
+          mine.ox = ox;
+          mine.oy = oy;
+          mine.oz = oz;
+          mine.dsx = dx;
+          mine.dsy = dy;
+          mine.dsz = dz;
+          const unsigned long long dqu = (unsigned long long)dq;
+          pk[cur * 32 + lane].x = (int)(uint32_t)dqu;
+          pk[cur * 32 + lane].y = (int)(uint32_t)(dqu >> 32);
+        }
+        n_rec += __popc(__ballot_sync(kFullMask, m != 0u));
+      }
+      // batch b-1's spins go to the lattice now that the producer has read it for batch b
+      if (b > 0) {
+        publish(Rp, acc_prev);
+        named_arrive(kBarDone + (cur ^ 1));
+      } else {
+        __syncwarp();
+      }
       // would a step to bcur + 1 / bcur - 1 be accepted at this move, given no change of bin since k_seg
       auto pass_masks = [&](uint32_t& up, uint32_t& down) {
         const long long ln = lng_seg + (long long)(lane - k_seg) * lnf_eff;
@@ -524,8 +624,8 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       // ---- sequential part, in branch-free blocks of 8 moves ----
       // Within a bin the state is frac = Efx - (bcur << 32) in [0, 2^32).  A move in the same bin is
       // accepted (frac += dq); a step to a neighbouring bin is accepted iff its pass bit is set, an
-      // event handled out of line, like re-evaluations and jumps of two or more bins.  The common
-      // path uses no compare-and-select: masks come from sign bits.
+      // event handled out of line, like moves that meet an accepted move of this batch and jumps
+      // of two or more bins.  The common path uses no compare-and-select: masks come from sign bits.
       const int4* P4 = pk + cur * 32;
       uint32_t frac = (uint32_t)Efx;
       int k = 0;
@@ -554,7 +654,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
           const uint32_t up = (uint32_t)(((th - 1) | (1 - th)) >> 31);       // all ones iff th != 1
           const uint32_t dn = (uint32_t)(((th + 1) | (-1 - th)) >> 31);      // all ones iff th != -1
           const uint32_t far = nz & up & dn;                                  // |th| >= 2
-          const uint32_t need = (need_prev & bit) | (cc & acc_cur & ~bit);
+          const uint32_t need = cc & acc_cur & ~bit;
           exc |= bit & (((~up) & up_mask) | ((~dn) & down_mask) | far | (need ? 0xffffffffu : 0u));
         }
         if (exc == 0u) {
@@ -569,38 +669,24 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         Efx = ((long long)bcur << 32) | frac;
         {
           const int kk = kx;
-          const Rec<false>& rk = rec[cur * 32 + kk];
+          Rec<false>& rk = Rc[kk];
           long long dq = rk.dq;
           const uint32_t bit = 1u << kk;
-          const bool need = ((need_prev & bit) | (rk.ccur & acc_cur)) != 0u;
-          if (need) {
-            // publish the accepted spins of this batch, then re-evaluate on the current lattice
-            const uint32_t pend = acc_cur & ~stored;
-            if ((pend >> lane) & 1u) {
-              sx[mine.site] = mine.nx;
-              sy[mine.site] = mine.ny;
-              sz[mine.site] = mine.nz;
-            }
-            stored |= pend;
-            __syncwarp();
-            const int site = rk.site;
-            int X, Y, Z;
-            bcc_coords(site, L, a.geo.divL, X, Y, Z);
-            float dEn;
-            if constexpr (NSH <= 3) {
-              // up to 26 neighbours: every lane evaluates the same field with the producer's
-              // arithmetic (broadcast loads, no reduction across lanes)
-              float hx, hy, hz;
-              uint32_t o0 = 0, o1 = 0;
-              field_one_lane<false, NSH, false>(sx, sy, sz, X, Y, Z, L, Jsh_r, hx, hy, hz, own, omask, o0, o1);
-              const float dx = rk.nx - sx[site], dy = rk.ny - sy[site], dz = rk.nz - sz[site];
-              dEn = -fmaf(dz, hz, fmaf(dy, hy, dx * hx));
-            } else {
-              // 50 neighbours: spread over the lanes, reduced by shuffles
-              dEn = delta_energy<false>(a, off_s, J_s, sx, sy, sz, site, X, Y, Z, rk.nx, rk.ny, rk.nz, lane, 32,
-                                        kFullMask);
-            }
+          const uint32_t m = rk.ccur & acc_cur;
+          if (m) {
+            // accepted moves of this batch around it (every lane computes the same values)
+            float hx = rk.hx, hy = rk.hy, hz = rk.hz, ox = rk.ox, oy = rk.oy, oz = rk.oz;
+            correct(Rc, m, rk.site, hx, hy, hz, ox, oy, oz);
+            const float dx = rk.nx - ox, dy = rk.ny - oy, dz = rk.nz - oz;
+            const float dEn = -fmaf(dz, hz, fmaf(dy, hy, dx * hx));
             dq = (long long)dq24_of(dEn, a.win) << 8;
+            __syncwarp();
+            if (lane == 0) {
+              rk.dsx = dx;
+              rk.dsy = dy;
+              rk.dsz = dz;
+            }
+            __syncwarp();
             ++n_rec;
           }
           const long long Ep = Efx + dq;
@@ -646,18 +732,13 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       // the batch's moves at the current bin
       lng_seg += (long long)(nvalid - k_seg) * lnf_eff;
       h_seg += hinc * (uint32_t)(nvalid - k_seg);
-      // accepted spins not yet written (no two share a site: a second one would have been
-      // re-evaluated, which publishes the first)
-      const uint32_t pend = acc_cur & ~stored;
-      if ((pend >> lane) & 1u) {
-        sx[mine.site] = mine.nx;
-        sy[mine.site] = mine.ny;
-        sz[mine.site] = mine.nz;
-      }
       n_acc += __popc(acc_cur);
       acc_prev = acc_cur;
-      __syncwarp();
-      named_arrive(kBarDone + cur);
+    }
+    // the last batch's spins
+    if (nb > 0) {
+      publish(rec + ((nb - 1) & 1) * 32, acc_prev);
+      named_arrive(kBarDone + ((nb - 1) & 1));
     }
     if (lane == 0 && !bad) {
       a.st.efx[slot] = Efx;

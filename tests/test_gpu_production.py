@@ -157,15 +157,20 @@ def test_initial_drive_cap_reports_timeout():
 
 
 @pytest.mark.parametrize("L,J,group_size", [(16, (1.0, 0.5), 1), (16, (1.0, 0.6, -0.05, -0.1), 1),
-                                            (12, (1.0, 0.5, 0.2), 2), (24, (1.0, 0.5), 1)])
+                                            (12, (1.0, 0.5, 0.2), 2), (24, (1.0, 0.5), 1),
+                                            (3, (1.0,), 1), (4, (1.0, 0.5), 1), (4, (1.0, 0.6, -0.05, -0.1), 1),
+                                            (6, (1.0, 0.5, 0.2), 1)])
 def test_running_energy_tracks_configuration_without_recompute(L, J, group_size):
     """With the periodic recomputation switched off, the fixed-point running energy built from the
     FP32 dE of every accepted move still equals the FP64 energy of the configuration (pins the
-    conflict detection of both walkers: a missed conflict leaves a stale dE behind)."""
+    conflict detection and the energy corrections of both walkers: a missed conflict or a wrong
+    correction leaves a stale dE behind).  The small lattices put almost every move of the
+    pipelined walker's 64 in flight next to another one."""
     N = 2 * L ** 3
-    g = rw.REWL(kind=rw.BCC, L=L, J=J, n_bins=N // 4, n_windows=8, walkers_per_window=2, lnf_final=1e-8,
-                seed=3, exchange_interval=10000, mode=rw.PRODUCTION, recompute_every=1000000,
-                group_size=group_size)
+    g = rw.REWL(kind=rw.BCC, L=L, J=J, n_bins=max(N // 4, 64), n_windows=8 if N >= 2000 else 3,
+                walkers_per_window=2, lnf_final=1e-8, seed=3, exchange_interval=10000, mode=rw.PRODUCTION,
+                recompute_every=1000000, group_size=group_size)
+    assert g.info()["pipelined"] == (1 if group_size == 1 else 0)
     g.run_intervals(5)
     w = g.walkers()
     Er = g.replica_energies()
