@@ -298,7 +298,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       r.ccur = ocur & ((1u << lane) - 1u);
       if constexpr (!kTraj) {
         const unsigned long long dqu = (unsigned long long)r.dq;
-        pk[cur * 32 + lane] = make_int4((int)(uint32_t)dqu, (int)(uint32_t)(dqu >> 32), (int)r.ccur, 0);
+        pk[cur * 32 + lane] = make_int4((int)(uint32_t)dqu, (int)(uint32_t)(dqu >> 32), (int)r.ccur, r.lu);
       }
       r.site = site;
       r.nx = nx;
@@ -526,9 +526,11 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       const int sh = r2 == 3 ? 0 : (r2 == 4 ? 1 : (r2 == 8 ? 2 : (r2 == 11 ? 3 : 4)));
       return sh < NSH ? Jsh_r[sh] : 0.0f;
     };
-    // field and old spin of a move at site p after the accepted moves m of record block R, in order
+    // field and old spin of a move at site p after the accepted moves m of record block R, in order;
+    // returns the moves among m that sit on site p (a later accepted move supersedes them)
     auto correct = [&](const Rec<false>* R, uint32_t m, int p, float& hx, float& hy, float& hz, float& ox, float& oy,
-                       float& oz) {
+                       float& oz) -> uint32_t {
+      uint32_t same = 0u;
       while (m) {
         const int j = __ffs(m) - 1;
         m &= m - 1u;
@@ -538,6 +540,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
           ox = rj.nx;
           oy = rj.ny;
           oz = rj.nz;
+          same |= 1u << j;
         } else {
           const float J = coupling(p, q);
           hx = fmaf(J, rj.dsx, hx);
@@ -545,13 +548,12 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
           hz = fmaf(J, rj.dsz, hz);
         }
       }
+      return same;
     };
-    // write the accepted spins of record block R (the last accepted move per site)
+    // write the accepted spins of record block R: acc minus the moves superseded on their site
     auto publish = [&](const Rec<false>* R, uint32_t acc) {
-      const Rec<false>& rp = R[lane];
-      const bool mine_acc = (acc >> lane) & 1u;
-      const uint32_t same = __match_any_sync(kFullMask, mine_acc ? rp.site : -1 - lane);
-      if (mine_acc && (same >> lane) == 1u) {
+      if ((acc >> lane) & 1u) {
+        const Rec<false>& rp = R[lane];
         sx[rp.site] = rp.nx;
         sy[rp.site] = rp.ny;
         sz[rp.site] = rp.nz;
@@ -562,20 +564,25 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
     // and histogram h_seg; after j more moves there, ln g = lng_seg + j ln f
     long long lng_seg = lng_in;
     uint32_t h_seg = h_in;
-    uint32_t acc_prev = 0;
+    uint32_t acc_prev = 0, pub_prev = 0;
     int n_rec = 0;
     long long n_acc = 0;
+    // Two ways through a batch, with the same decisions: branch-free blocks of 8 moves with the
+    // rare events out of line (wide bins), or one move at a time (narrow bins, where most moves
+    // change bin).  A batch with many events sends the next one down the sequential path, a
+    // sequential batch with few sends it back.
+    bool sequential = false;
     for (int b = 0; b < nb; ++b) {
       const int cur = b & 1;
       named_sync(kBarReady + cur);
       const int nvalid = bad ? 0 : (int)(moves - (long long)b * 32 < 32 ? moves - (long long)b * 32 : 32);
       int k_seg = 0;
-      uint32_t acc_cur = 0;
+      uint32_t acc_cur = 0, sup = 0;
+      int events = 0;
       Rec<false>* Rc = rec + cur * 32;
       const Rec<false>* Rp = rec + (cur ^ 1) * 32;
       // ---- parallel part: lane = move index ----
       Rec<false>& mine = Rc[lane];
-      const int my_lu = mine.lu;
       {
         // accepted moves of batch b-1 around this move: correct h and o, then dE
         const uint32_t m = lane < nvalid ? (mine.cprev & acc_prev) : 0u;
@@ -603,11 +610,12 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       }
       // batch b-1's spins go to the lattice now that the producer has read it for batch b
       if (b > 0) {
-        publish(Rp, acc_prev);
+        publish(Rp, pub_prev);
         named_arrive(kBarDone + (cur ^ 1));
       } else {
         __syncwarp();
       }
+      const int my_lu = mine.lu;
       // would a step to bcur + 1 / bcur - 1 be accepted at this move, given no change of bin since k_seg
       auto pass_masks = [&](uint32_t& up, uint32_t& down) {
         const long long ln = lng_seg + (long long)(lane - k_seg) * lnf_eff;
@@ -619,125 +627,149 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         up = __ballot_sync(kFullMask, pu);
         down = __ballot_sync(kFullMask, pd);
       };
-      uint32_t up_mask, down_mask;
-      pass_masks(up_mask, down_mask);
-      // ---- sequential part, in branch-free blocks of 8 moves ----
-      // Within a bin the state is frac = Efx - (bcur << 32) in [0, 2^32).  A move in the same bin is
-      // accepted (frac += dq); a step to a neighbouring bin is accepted iff its pass bit is set, an
-      // event handled out of line, like moves that meet an accepted move of this batch and jumps
-      // of two or more bins.  The common path uses no compare-and-select: masks come from sign bits.
-      const int4* P4 = pk + cur * 32;
-      uint32_t frac = (uint32_t)Efx;
-      int k = 0;
-      while (k < nvalid) {
-        const uint32_t acc0 = acc_cur;
-        uint32_t exc = 0;
-        int4 q[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) q[u] = P4[(k + u) & 31];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int kk = k + u;
-          if (lane == u) fhist[u] = frac;
-          const uint32_t lo = (uint32_t)q[u].x;
-          const int hi = q[u].y;
-          const uint32_t cc = (uint32_t)q[u].z;
-          const uint32_t vmask = (uint32_t)((kk - nvalid) >> 31);          // all ones while kk < nvalid
-          const uint32_t bit = (1u << (kk & 31)) & vmask;
-          const uint32_t t_lo = frac + lo;
-          const uint32_t carry = ((frac & lo) | ((frac | lo) & ~t_lo)) >> 31;
-          const int th = hi + (int)carry;                                     // high word of frac + dq: bins moved
-          const uint32_t nz = (uint32_t)((th | -th) >> 31);                   // all ones iff th != 0
-          const uint32_t stay = ~nz & vmask;
-          frac = (t_lo & stay) | (frac & ~stay);
-          acc_cur |= bit & stay;
-          const uint32_t up = (uint32_t)(((th - 1) | (1 - th)) >> 31);       // all ones iff th != 1
-          const uint32_t dn = (uint32_t)(((th + 1) | (-1 - th)) >> 31);      // all ones iff th != -1
-          const uint32_t far = nz & up & dn;                                  // |th| >= 2
-          const uint32_t need = cc & acc_cur & ~bit;
-          exc |= bit & (((~up) & up_mask) | ((~dn) & down_mask) | far | (need ? 0xffffffffu : 0u));
-        }
-        if (exc == 0u) {
-          k += 8;
-          continue;
-        }
-        // first exceptional move: the block's moves before it stand; restore the state there
-        const int kx = __ffs(exc) - 1;
-        __syncwarp();
-        frac = fhist[kx - k];
-        acc_cur = acc0 | (acc_cur & ((1u << kx) - 1u));
-        Efx = ((long long)bcur << 32) | frac;
-        {
-          const int kk = kx;
+      uint32_t up_mask = 0, down_mask = 0;
+      // One move kk with increment dq (corrected first if it meets an accepted move of this batch):
+      // Metropolis step on ln g, bin bookkeeping; every lane computes the same values.  Returns
+      // whether a bin change happened (the pass masks are then stale).
+      auto resolve = [&](const int kk, long long dq, const uint32_t ccur_w, const int lu) -> bool {
+        const uint32_t m = ccur_w & acc_cur;
+        uint32_t same = 0u;
+        if (m) {
           Rec<false>& rk = Rc[kk];
-          long long dq = rk.dq;
-          const uint32_t bit = 1u << kk;
-          const uint32_t m = rk.ccur & acc_cur;
-          if (m) {
-            // accepted moves of this batch around it (every lane computes the same values)
-            float hx = rk.hx, hy = rk.hy, hz = rk.hz, ox = rk.ox, oy = rk.oy, oz = rk.oz;
-            correct(Rc, m, rk.site, hx, hy, hz, ox, oy, oz);
-            const float dx = rk.nx - ox, dy = rk.ny - oy, dz = rk.nz - oz;
-            const float dEn = -fmaf(dz, hz, fmaf(dy, hy, dx * hx));
-            dq = (long long)dq24_of(dEn, a.win) << 8;
-            __syncwarp();
-            if (lane == 0) {
-              rk.dsx = dx;
-              rk.dsy = dy;
-              rk.dsz = dz;
-            }
-            __syncwarp();
-            ++n_rec;
+          float hx = rk.hx, hy = rk.hy, hz = rk.hz, ox = rk.ox, oy = rk.oy, oz = rk.oz;
+          same = correct(Rc, m, rk.site, hx, hy, hz, ox, oy, oz);
+          const float dx = rk.nx - ox, dy = rk.ny - oy, dz = rk.nz - oz;
+          const float dEn = -fmaf(dz, hz, fmaf(dy, hy, dx * hx));
+          dq = (long long)dq24_of(dEn, a.win) << 8;
+          __syncwarp();
+          if (lane == 0) {
+            rk.dsx = dx;
+            rk.dsy = dy;
+            rk.dsz = dz;
           }
-          const long long Ep = Efx + dq;
-          const int db = fx_bin(Ep) - bcur;
-          const int bp = bcur + db;
-          const long long lng_now = lng_seg + (long long)(kk - k_seg) * lnf_eff;
-          bool acc;
-          if (db == 0) {
-            acc = true;
-          } else {
-            const int rel = bp - wlo;
-            acc = false;
-            if ((unsigned)rel < (unsigned)W) {
-              const long long lngp = db == 1 ? lng_p : (db == -1 ? lng_m : (long long)lng_s[rel]);
-              const long long d = lng_now - lngp;
-              const int e20 = d < -(1LL << 51) ? (int)0x80000000 : (int)(d >> 20);
-              acc = d >= 0 || rk.lu < e20;
-              if (acc) {
-                // leave bcur: write it back, shift the neighbour cache, start a new segment
-                lng_s[bcur - wlo] = (Lng)lng_now;
-                H_s[bcur - wlo] = h_seg + hinc * (uint32_t)(kk - k_seg);
-                if (db == 1) lng_m = lng_now;
-                if (db == -1) lng_p = lng_now;
-                lng_seg = lngp;
-                h_seg = H_s[rel];
-                k_seg = kk;
-                bcur = bp;
-                if (db != -1) lng_p = bcur + 1 < wlo + W ? (long long)lng_s[bcur + 1 - wlo] : 0;
-                if (db != 1) lng_m = bcur - 1 >= wlo ? (long long)lng_s[bcur - 1 - wlo] : 0;
-                pass_masks(up_mask, down_mask);
-              }
-            }
-          }
-          if (acc) {
-            Efx = Ep;
-            acc_cur |= bit;
-          }
-          frac = (uint32_t)Efx;
+          __syncwarp();
+          ++n_rec;
+          ++events;
         }
-        k = kx + 1;
+        const long long Ep = Efx + dq;
+        const int db = fx_bin(Ep) - bcur;
+        bool acc = true, moved = false;
+        if (db != 0) {
+          const int bp = bcur + db;
+          const int rel = bp - wlo;
+          acc = false;
+          if ((unsigned)rel < (unsigned)W) {
+            const long long lng_now = lng_seg + (long long)(kk - k_seg) * lnf_eff;
+            const long long lngp = db == 1 ? lng_p : (db == -1 ? lng_m : (long long)lng_s[rel]);
+            const long long d = lng_now - lngp;
+            const int e20 = d < -(1LL << 51) ? (int)0x80000000 : (int)(d >> 20);
+            acc = d >= 0 || lu < e20;
+            if (acc) {
+              // leave bcur: write it back, shift the neighbour cache, start a new segment
+              lng_s[bcur - wlo] = (Lng)lng_now;
+              H_s[bcur - wlo] = h_seg + hinc * (uint32_t)(kk - k_seg);
+              if (db == 1) lng_m = lng_now;
+              if (db == -1) lng_p = lng_now;
+              lng_seg = lngp;
+              h_seg = H_s[rel];
+              k_seg = kk;
+              bcur = bp;
+              if (db != -1) lng_p = bcur + 1 < wlo + W ? (long long)lng_s[bcur + 1 - wlo] : 0;
+              if (db != 1) lng_m = bcur - 1 >= wlo ? (long long)lng_s[bcur - 1 - wlo] : 0;
+              moved = true;
+            }
+          }
+        }
+        if (acc) {
+          Efx = Ep;
+          acc_cur |= 1u << kk;
+          sup |= same;   // earlier accepted moves on this site are no longer the site's spin
+        }
+        // the events that leave a block of the branch-free path: corrections (counted above),
+        // accepted bin changes, jumps of two or more bins
+        events += (moved || db > 1 || db < -1) ? 1 : 0;
+        return moved;
+      };
+      const int4* P4 = pk + cur * 32;
+      if (sequential) {
+        // ---- sequential part, one move at a time ----
+        int4 w = P4[0];
+        for (int kk = 0; kk < nvalid; ++kk) {
+          const int4 wn = P4[(kk + 1) & 31];
+          const long long dq = (long long)(((unsigned long long)(uint32_t)w.y << 32) | (uint32_t)w.x);
+          resolve(kk, dq, (uint32_t)w.z, w.w);
+          w = wn;
+        }
+        sequential = events >= 4;
+      } else {
+        // ---- sequential part, in branch-free blocks of 8 moves ----
+        // Within a bin the state is frac = Efx - (bcur << 32) in [0, 2^32).  A move in the same bin
+        // is accepted (frac += dq); a step to a neighbouring bin is accepted iff its pass bit is
+        // set, an event handled out of line, like moves that meet an accepted move of this batch
+        // and jumps of two or more bins.  The common path uses no compare-and-select: masks come
+        // from sign bits.
+        pass_masks(up_mask, down_mask);
+        uint32_t frac = (uint32_t)Efx;
+        int k = 0;
+        int n_out = 0;
+        while (k < nvalid) {
+          const uint32_t acc0 = acc_cur;
+          uint32_t exc = 0;
+          int4 q[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) q[u] = P4[(k + u) & 31];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int kk = k + u;
+            if (lane == u) fhist[u] = frac;
+            const uint32_t lo = (uint32_t)q[u].x;
+            const int hi = q[u].y;
+            const uint32_t cc = (uint32_t)q[u].z;
+            const uint32_t vmask = (uint32_t)((kk - nvalid) >> 31);          // all ones while kk < nvalid
+            const uint32_t bit = (1u << (kk & 31)) & vmask;
+            const uint32_t t_lo = frac + lo;
+            const uint32_t carry = ((frac & lo) | ((frac | lo) & ~t_lo)) >> 31;
+            const int th = hi + (int)carry;                                     // high word of frac + dq: bins moved
+            const uint32_t nz = (uint32_t)((th | -th) >> 31);                   // all ones iff th != 0
+            const uint32_t stay = ~nz & vmask;
+            frac = (t_lo & stay) | (frac & ~stay);
+            acc_cur |= bit & stay;
+            const uint32_t up = (uint32_t)(((th - 1) | (1 - th)) >> 31);       // all ones iff th != 1
+            const uint32_t dn = (uint32_t)(((th + 1) | (-1 - th)) >> 31);      // all ones iff th != -1
+            const uint32_t far = nz & up & dn;                                  // |th| >= 2
+            const uint32_t need = cc & acc_cur & ~bit;
+            exc |= bit & (((~up) & up_mask) | ((~dn) & down_mask) | far | (need ? 0xffffffffu : 0u));
+          }
+          if (exc == 0u) {
+            k += 8;
+            continue;
+          }
+          // first exceptional move: the block's moves before it stand; restore the state there
+          const int kx = __ffs(exc) - 1;
+          __syncwarp();
+          frac = fhist[kx - k];
+          acc_cur = acc0 | (acc_cur & ((1u << kx) - 1u));
+          Efx = ((long long)bcur << 32) | frac;
+          const int4 wx = P4[kx];
+          const long long dq = (long long)(((unsigned long long)(uint32_t)wx.y << 32) | (uint32_t)wx.x);
+          if (resolve(kx, dq, (uint32_t)wx.z, wx.w)) pass_masks(up_mask, down_mask);
+          frac = (uint32_t)Efx;
+          ++n_out;
+          k = kx + 1;
+        }
+        Efx = ((long long)bcur << 32) | frac;
+        sequential = n_out >= 6;
       }
-      Efx = ((long long)bcur << 32) | frac;
       // the batch's moves at the current bin
       lng_seg += (long long)(nvalid - k_seg) * lnf_eff;
       h_seg += hinc * (uint32_t)(nvalid - k_seg);
       n_acc += __popc(acc_cur);
       acc_prev = acc_cur;
+      pub_prev = acc_cur & ~sup;
     }
     // the last batch's spins
     if (nb > 0) {
-      publish(rec + ((nb - 1) & 1) * 32, acc_prev);
+      publish(rec + ((nb - 1) & 1) * 32, pub_prev);
       named_arrive(kBarDone + ((nb - 1) & 1));
     }
     if (lane == 0 && !bad) {
