@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--intervals", type=int, default=20, help="exchange intervals per step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--jobs-per-size", type=int, default=16,
+                   help="batch64: jobs per lattice size (16 gives the 64-job workload; smaller for profiling)")
     p.add_argument("--workload", default="single", choices=["single", "batch64", "warmstart"],
                    help="single: one job, bcc L=16 (the headline line); batch64: 64 jobs of bcc L=8..20 "
                         "in one persistent launch; warmstart: learned warm start versus plain REWL")
@@ -68,6 +70,16 @@ def dist_init(n):
             torch.cuda.set_device(local)
         dist.init_process_group(backend=backend)
     return rank, world, local
+
+
+def replica_seed(rank):
+    """Every rank runs its own replica of the workload (weak scaling, no data-path collective)."""
+    return 1 + rank
+
+
+def aggregate_rate(units_per_rank, world, max_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (max_ms * 1e-3)
 
 
 def barrier(world):
@@ -253,11 +265,11 @@ def run_batch64(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
     I = args.intervals
-    specs = workloads.batch64_jobs()
+    specs = workloads.batch64_jobs(jobs_per_size=args.jobs_per_size)
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         jobs = [rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, group_size=1, stream=stream,
-                        **dict(s, seed=s["seed"] + 100000 * rank)) for s in specs]
+                        **dict(s, seed=s["seed"] + 100000 * (replica_seed(rank) - 1))) for s in specs]
         batch = rw.Batch(jobs, stream=stream)
     setup_s = time.perf_counter() - t0
     tune = batch.autotune(trial_moves=2000)
@@ -284,7 +296,7 @@ def run_batch64(args):
     barrier(world)
     clk = clocks.stop()
     total_ms = all_max(sum(step_ms), world)
-    value = moves_per_step * args.steps * world / (total_ms * 1e-3)
+    value = aggregate_rate(moves_per_step * args.steps, world, total_ms)
     info = batch.info()
     if rank == 0:
         line = {
@@ -292,7 +304,8 @@ def run_batch64(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp32 spins/dE + int64 fixed-point ln g/energy",
             "data": "synthetic",
-            "config": {"workload": "64 REWL jobs, bcc L in {8,12,16,20} x 16, J1=1 J2~U[0.2,0.6] J3~U[-0.1,0.1], "
+            "config": {"workload": f"{len(specs)} REWL jobs, bcc L in {{8,12,16,20}} x {args.jobs_per_size}, "
+                                   "J1=1 J2~U[0.2,0.6] J3~U[-0.1,0.1], "
                                    "N/4 bins over [E_gs,0], 8/16/24/32 windows x 4 walkers, exchange every 1e4 moves",
                        "walker_slots": S, "intervals_per_step": I, "moves_per_step": moves_per_step * world,
                        "l2": "flushed between steps (256 MB write)", "graph": True,
@@ -366,7 +379,7 @@ def main():
     stream = torch.cuda.current_stream()
     I = args.intervals
 
-    sim = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, seed=1 + rank, stream=stream, **WORKLOAD)
+    sim = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, seed=replica_seed(rank), stream=stream, **WORKLOAD)
     sim.init_walkers()
     S, B = sim.n_slots, sim.B
     moves_per_step = S * WORKLOAD["exchange_interval"] * I
@@ -411,7 +424,7 @@ def main():
     c1 = sim.counters()
 
     total_ms = all_max(sum(step_ms), world)
-    value = moves_per_step * args.steps * world / (total_ms * 1e-3)
+    value = aggregate_rate(moves_per_step * args.steps, world, total_ms)
     acc_rate = (c1["accepts"] - c0["accepts"]) / max(1, c1["moves"] - c0["moves"])
     rec_rate = (c1["recomputes"] - c0["recomputes"]) / max(1, c1["moves"] - c0["moves"])
 
