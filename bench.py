@@ -49,9 +49,10 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--jobs-per-size", type=int, default=16,
                    help="batch64: jobs per lattice size (16 gives the 64-job workload; smaller for profiling)")
-    p.add_argument("--workload", default="single", choices=["single", "batch64", "warmstart"],
+    p.add_argument("--workload", default="single", choices=["single", "batch64", "warmstart", "weak-scaling"],
                    help="single: one job, bcc L=16 (the headline line); batch64: 64 jobs of bcc L=8..20 "
-                        "in one persistent launch; warmstart: learned warm start versus plain REWL")
+                        "in one persistent launch; warmstart: learned warm start versus plain REWL; "
+                        "weak-scaling: moves to finish the first WL iteration versus L")
     return p.parse_args()
 
 
@@ -362,6 +363,49 @@ def run_warmstart(args):
     return 0
 
 
+def run_weak_scaling(args):
+    """Trial moves per walker to finish the first Wang-Landau iteration versus lattice size (the
+    paper's weak-scaling measure, Sec. 5, Fig. 3): windows of 64 bins at 75 % overlap, one walker
+    each, their number growing with N (bcc L = 4..12, 5 to 213 windows), against one serial walker
+    over the same range (L <= 8).  Range [0.6 E_gs, 0] with one bin per spin, J = (1, 0.5).  All
+    jobs run in one batch; each leaves the work list when its walkers have halved ln f once."""
+    import numpy as np
+    import torch
+    import paper_1411_4212_gb300 as rw
+    from paper_1411_4212_gb300 import warmstart
+    rank, world, local = dist_init(args.gpus)
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    J = (1.0, 0.5)
+    sizes, serial_sizes = (4, 6, 8, 10, 12), (4, 6, 8)
+    jobs = [warmstart.first_iteration_job(L, J, seed=100 + L) for L in sizes]
+    jobs += [warmstart.first_iteration_job(L, J, seed=200 + L, serial=True) for L in serial_sizes]
+    t0 = time.perf_counter()
+    with rw.Batch(jobs) as b:
+        ok, done = b.run_to_convergence(max_intervals=20000, check_every=4)
+    wall = time.perf_counter() - t0
+    rows = []
+    for j, L in zip(jobs, list(sizes) + list(serial_sizes)):
+        w = j.walkers()
+        rows.append({"L": L, "N": 2 * L ** 3, "windows": j.h, "bins_per_window": j.W,
+                     "moves_per_walker": float(w["steps"].mean()), "first_iteration_done": bool(np.all(w["stage"] >= 1)),
+                     "serial": j.h == 1})
+        j.close()
+    rewl = [r for r in rows if not r["serial"]]
+    line = {
+        "metric": "trial moves per walker to finish the first WL iteration, largest / smallest lattice",
+        "value": rewl[-1]["moves_per_walker"] / rewl[0]["moves_per_walker"], "unit": "ratio",
+        "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": "weak scaling: bcc L=4..12, J=(1,0.5), range [0.6 E_gs, 0], one bin per spin, "
+                               "windows of ~64 bins at 75% overlap (h grows with N), 1 walker per window; "
+                               "serial: one walker over the whole range", "all_done": bool(ok), "wall_s": wall},
+        "rows": rows,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -370,6 +414,8 @@ def main():
         return run_batch64(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "weak-scaling":
+        return run_weak_scaling(args)
     import torch
     import paper_1411_4212_gb300 as rw
 

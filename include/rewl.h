@@ -241,6 +241,13 @@ rewl_status rewl_get_spins(rewl_handle* h, double* spins);
 /* Replica-exchange counters per window pair: host [n_windows - 1] each. */
 rewl_status rewl_get_exchange_counts(rewl_handle* h, int64_t* attempts, int64_t* accepts);
 
+/* Replica round trips (Sec. 5, Fig. 1), per configuration r (host arrays [S], either may be NULL):
+ * counts[r] = round trips completed, last[r] = extreme window r was found in last (-1 none, 0 the
+ * lowest window, 1 the highest).  A round trip is completed when a configuration is found in the
+ * lowest window after having been found in the highest; the configurations of both extreme windows
+ * are looked at before and after every replica-exchange round.  With one window nothing is counted. */
+rewl_status rewl_get_round_trips(rewl_handle* h, int64_t* counts, int32_t* last);
+
 /* Totals over all walkers. */
 rewl_status rewl_get_counters(rewl_handle* h, rewl_counters* out);
 

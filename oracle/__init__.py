@@ -67,6 +67,7 @@ def lib():
         L.ro_get_walkers.argtypes = [C.c_void_p, dp, up, dp, ip, dp, ip, lp, ip, lp, lp]
         L.ro_get_spins.argtypes = [C.c_void_p, dp]
         L.ro_get_exchange_counts.argtypes = [C.c_void_p, lp, lp]
+        L.ro_get_round_trips.argtypes = [C.c_void_p, lp, ip]
         L.ro_max_drift.argtypes = [C.c_void_p]
         L.ro_max_drift.restype = C.c_double
         L.ro_exchange_index.argtypes = [C.c_void_p]
@@ -281,6 +282,14 @@ class OracleREWL:
         b = np.zeros(n, dtype=np.int64)
         lib().ro_get_exchange_counts(self._h, a, b)
         return a[: self.h - 1], b[: self.h - 1]
+
+    def round_trips(self):
+        """(round trips completed [S], extreme window seen last [S]: -1 none, 0 lowest, 1 highest)
+        per replica."""
+        c = np.zeros(self.n_slots, dtype=np.int64)
+        last = np.zeros(self.n_slots, dtype=np.int32)
+        lib().ro_get_round_trips(self._h, c, last)
+        return c, last
 
     def max_drift(self):
         return lib().ro_max_drift(self._h)

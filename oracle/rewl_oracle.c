@@ -218,6 +218,8 @@ struct ro_sim {
   int64_t* accepts;
   int64_t* steps;
   int64_t* init_moves;
+  int32_t* rt_last; /* [S] per replica: extreme window seen last (-1 none, 0 lowest, 1 highest) */
+  int64_t* rt_count;/* [S] per replica: round trips completed */
   int64_t* ex_att;  /* [h-1] */
   int64_t* ex_acc;
   int64_t ex_index;
@@ -361,9 +363,12 @@ int ro_create(const ro_params* p, ro_sim** out, char* err, int errlen) {
   s->accepts = (int64_t*)calloc(S, sizeof(int64_t));
   s->steps = (int64_t*)calloc(S, sizeof(int64_t));
   s->init_moves = (int64_t*)calloc(S, sizeof(int64_t));
+  s->rt_last = (int32_t*)malloc(sizeof(int32_t) * S);
+  s->rt_count = (int64_t*)calloc(S, sizeof(int64_t));
+  if (s->rt_last) for (size_t r = 0; r < S; ++r) s->rt_last[r] = -1;
   s->ex_att = (int64_t*)calloc((size_t)(s->h > 1 ? s->h - 1 : 1), sizeof(int64_t));
   s->ex_acc = (int64_t*)calloc((size_t)(s->h > 1 ? s->h - 1 : 1), sizeof(int64_t));
-  if (!s->spins || !s->lng || !s->H || !s->E || !s->bin || !s->perm || !s->lnf) {
+  if (!s->spins || !s->lng || !s->H || !s->E || !s->bin || !s->perm || !s->lnf || !s->rt_last || !s->rt_count) {
     set_err(err, errlen, "out of memory"); ro_destroy(s); return -1;
   }
 
@@ -399,7 +404,7 @@ void ro_destroy(ro_sim* s) {
   if (!s) return;
   free(s->nbr); free(s->Jt); free(s->starts); free(s->spins); free(s->lng); free(s->H);
   free(s->E); free(s->bin); free(s->perm); free(s->lnf); free(s->stage); free(s->accepts);
-  free(s->steps); free(s->init_moves); free(s->ex_att); free(s->ex_acc);
+  free(s->steps); free(s->init_moves); free(s->ex_att); free(s->ex_acc); free(s->rt_last); free(s->rt_count);
   free(s);
 }
 
@@ -607,7 +612,21 @@ int ro_run_moves_only(ro_sim* s, int64_t moves_per_walker) {
 /* counter (t lo, t hi, 3, a).  On acceptance the slots swap configurations (replica index and  */
 /* energy); ln g and H stay with the slots.                                                    */
 /* ------------------------------------------------------------------------------------------- */
+/* Replica round trips (Sec. 5, Fig. 1): a replica completes one when it is found in the lowest
+   window after having been found in the highest.  The replicas of both extreme windows are looked
+   at before and after every exchange round (looking twice at the same state changes nothing). */
+static void observe_extremes(ro_sim* s) {
+  if (s->h < 2) return;
+  for (int a = 0; a < s->m; ++a) {
+    int r = s->perm[a];
+    if (s->rt_last[r] == 1) s->rt_count[r] += 1;
+    s->rt_last[r] = 0;
+    s->rt_last[s->perm[(s->h - 1) * s->m + a]] = 1;
+  }
+}
+
 int ro_exchange(ro_sim* s) {
+  observe_extremes(s);
   uint64_t t = (uint64_t)s->ex_index;
   int m = s->m;
   int shift = (int)((t / 2u) % (uint64_t)m);
@@ -640,6 +659,7 @@ int ro_exchange(ro_sim* s) {
       }
     }
   }
+  observe_extremes(s);
   s->ex_index += 1;
   return 0;
 }
@@ -855,6 +875,11 @@ void ro_get_exchange_counts(const ro_sim* s, int64_t* attempts, int64_t* accepts
   if (n <= 0) return;
   if (attempts) memcpy(attempts, s->ex_att, sizeof(int64_t) * (size_t)n);
   if (accepts) memcpy(accepts, s->ex_acc, sizeof(int64_t) * (size_t)n);
+}
+
+void ro_get_round_trips(const ro_sim* s, int64_t* counts, int32_t* last) {
+  if (counts) memcpy(counts, s->rt_count, sizeof(int64_t) * (size_t)s->S);
+  if (last) memcpy(last, s->rt_last, sizeof(int32_t) * (size_t)s->S);
 }
 
 double ro_max_drift(const ro_sim* s) { return s->max_drift; }

@@ -92,6 +92,9 @@ void ro_get_walkers(const ro_sim* s, double* lng /*[S][W]*/, uint32_t* H /*[S][W
                     int64_t* steps /*[S]*/, int64_t* init_moves /*[S]*/);
 void ro_get_spins(const ro_sim* s, double* spins /*[R][3][N]*/);
 void ro_get_exchange_counts(const ro_sim* s, int64_t* attempts /*[h-1]*/, int64_t* accepts);
+/* Round trips per replica [S] and the extreme window each replica was found in last (-1 none,
+   0 lowest, 1 highest); either pointer may be NULL. */
+void ro_get_round_trips(const ro_sim* s, int64_t* counts, int32_t* last);
 double ro_max_drift(const ro_sim* s);
 int64_t ro_exchange_index(const ro_sim* s);
 /* overwrite every walker's ln g with lng0[b] (global bins) and set ln f */

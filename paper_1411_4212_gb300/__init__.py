@@ -134,6 +134,7 @@ def load_library(path=LIB_PATH):
         "rewl_get_walkers": ([_vp] + [_vp] * 10, st),
         "rewl_get_spins": ([_vp, _vp], st),
         "rewl_get_exchange_counts": ([_vp, _vp, _vp], st),
+        "rewl_get_round_trips": ([_vp, _vp, _vp], st),
         "rewl_get_counters": ([_vp, C.POINTER(Counters)], st),
         "rewl_get_neighbours": ([_vp, _vp, _vp], st),
         "rewl_replica_energies": ([_vp, _vp], st),
@@ -347,6 +348,14 @@ class REWL:
         b = np.zeros(n, dtype=np.int64)
         _check(self._lib.rewl_get_exchange_counts(self._h, _ptr(a), _ptr(b)), self._h)
         return a[: self.h - 1], b[: self.h - 1]
+
+    def round_trips(self):
+        """(round trips completed [S], extreme window seen last [S]: -1 none, 0 lowest, 1 highest)
+        per configuration."""
+        c = np.zeros(self.n_slots, dtype=np.int64)
+        last = np.zeros(self.n_slots, dtype=np.int32)
+        _check(self._lib.rewl_get_round_trips(self._h, _ptr(c), _ptr(last)), self._h)
+        return c, last
 
     def counters(self):
         c = Counters()

@@ -60,6 +60,8 @@ struct rewl_handle {
   double* d_drift = nullptr;
   int32_t* d_ctrl = nullptr;
   long long* d_ex_index = nullptr;
+  int32_t* d_rt_last = nullptr;
+  long long* d_rt_count = nullptr;
   unsigned long long* d_ex_att = nullptr;
   unsigned long long* d_ex_acc = nullptr;
   int32_t* d_starts = nullptr;
@@ -185,6 +187,8 @@ WalkerState state_of(rewl_handle* h) {
   s.drift = h->d_drift;
   s.ctrl = h->d_ctrl;
   s.ex_index = h->d_ex_index;
+  s.rt_last = h->d_rt_last;
+  s.rt_count = h->d_rt_count;
   s.ex_att = h->d_ex_att;
   s.ex_acc = h->d_ex_acc;
   return s;
@@ -517,6 +521,8 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   A(&h->d_drift, S);
   A(&h->d_ctrl, 4);
   A(&h->d_ex_index, 1);
+  A(&h->d_rt_last, S);
+  A(&h->d_rt_count, S);
   A(&h->d_ex_att, std::max(h->h - 1, 1));
   A(&h->d_ex_acc, std::max(h->h - 1, 1));
   A(&h->d_starts, h->h);
@@ -587,6 +593,8 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   zero(h->d_drift, S * sizeof(double));
   zero(h->d_ctrl, 4 * sizeof(int32_t));
   zero(h->d_ex_index, sizeof(long long));
+  if (ce == cudaSuccess) ce = cudaMemset(h->d_rt_last, 0xff, S * sizeof(int32_t));   // -1: no extreme seen yet
+  zero(h->d_rt_count, S * sizeof(long long));
   zero(h->d_ex_att, std::max(h->h - 1, 1) * sizeof(unsigned long long));
   zero(h->d_ex_acc, std::max(h->h - 1, 1) * sizeof(unsigned long long));
   up(h->d_starts, h->starts.data(), h->h * sizeof(int32_t));
@@ -1107,6 +1115,16 @@ rewl_status rewl_get_exchange_counts(rewl_handle* h, int64_t* attempts, int64_t*
   const size_t n = h->h - 1;
   if (attempts) CUDA_TRY(h, cudaMemcpyAsync(attempts, h->d_ex_att, n * 8, cudaMemcpyDeviceToHost, h->stream));
   if (accepts) CUDA_TRY(h, cudaMemcpyAsync(accepts, h->d_ex_acc, n * 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return REWL_OK;
+}
+
+rewl_status rewl_get_round_trips(rewl_handle* h, int64_t* counts, int32_t* last) {
+  rewl_status s = check_ready(h);
+  if (s != REWL_OK) return s;
+  const size_t S = h->S;
+  if (counts) CUDA_TRY(h, cudaMemcpyAsync(counts, h->d_rt_count, S * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (last) CUDA_TRY(h, cudaMemcpyAsync(last, h->d_rt_last, S * 4, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return REWL_OK;
 }

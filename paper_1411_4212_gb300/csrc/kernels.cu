@@ -18,9 +18,28 @@ namespace rewl {
 // the configuration index and the energy; ln g and H stay with the slots.  One CTA, so the round
 // counter is read once and advanced after every pair is done.
 // ------------------------------------------------------------------------------------------------
+// Replica round trips (Sec. 5, Fig. 1): a configuration completes one when it is found in the
+// lowest window after having been found in the highest.  The configurations of both extreme
+// windows are looked at before and after every round (looking twice at one state changes nothing);
+// each configuration sits in one slot, so the threads touch distinct entries.
+__device__ __forceinline__ void observe_extremes(const ExchangeArgs& a) {
+  const int h = a.win.h, m = a.win.m;
+  if (h < 2) return;
+  for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) {
+    if (i < m) {
+      const int r = a.st.perm[i];
+      if (a.st.rt_last[r] == 1) a.st.rt_count[r] += 1;
+      a.st.rt_last[r] = 0;
+    } else {
+      a.st.rt_last[a.st.perm[(h - 1) * m + (i - m)]] = 1;
+    }
+  }
+}
+
 __device__ __forceinline__ void exchange_block(const ExchangeArgs& a) {
   __shared__ long long t_s;
   if (threadIdx.x == 0) t_s = *a.st.ex_index;
+  observe_extremes(a);
   __syncthreads();
   const long long t = t_s;
   const int h = a.win.h, m = a.win.m, W = a.win.W;
@@ -82,6 +101,7 @@ __device__ __forceinline__ void exchange_block(const ExchangeArgs& a) {
     }
   }
   __syncthreads();
+  observe_extremes(a);
   if (threadIdx.x == 0) *a.st.ex_index = t + 1;
 }
 

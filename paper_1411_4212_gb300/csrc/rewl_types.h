@@ -59,6 +59,8 @@ struct WalkerState {
   double* drift;                       // [S] largest |running E - recomputed E|
   int32_t* ctrl;                       // [0] error code, [1] halved counter, [2] done counter
   long long* ex_index;                 // replica-exchange rounds done (device counter)
+  int32_t* rt_last;                    // [S] per configuration: extreme window seen last (-1, 0 lowest, 1 highest)
+  long long* rt_count;                 // [S] per configuration: round trips completed
   unsigned long long* ex_att;          // [h-1]
   unsigned long long* ex_acc;          // [h-1]
 };

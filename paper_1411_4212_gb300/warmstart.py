@@ -133,3 +133,15 @@ def warm_vs_cold(net, L, couplings, lnf_final=1e-5, replicas=2, lnf0=LNF0_WARM, 
         for j in cs + ws:
             j.close()
     return ok, out, wall
+
+
+def first_iteration_job(L, J, seed, window_bins=64, overlap=0.75, exchange_interval=4000, serial=False):
+    """The first Wang-Landau iteration (ln f 1 -> 1/2) as a job that converges at ln f < 0.9: the
+    restricted range with one bin per spin, windows of about `window_bins` bins at `overlap`, their
+    number growing with the lattice (the paper's weak-scaling set-up, Sec. 5, Fig. 3), one walker per
+    window; serial=True puts one walker over the whole range instead."""
+    N = 2 * L ** 3
+    h = 1 if serial else max(2, int(round(1 + (N / window_bins - 1) / (1 - overlap))))
+    return REWL(kind=BCC, mode=PRODUCTION, L=L, J=J, e_min=0.6 * ground_state(L, J), e_max=0.0, n_bins=N,
+                n_windows=h, walkers_per_window=1, overlap=overlap if h > 1 else 0.0, flatness=0.8,
+                lnf_final=0.9, seed=seed, exchange_interval=exchange_interval, group_size=1)

@@ -35,3 +35,6 @@ def assert_same_state(gpu, orc, spins=True):
     ag, bg = gpu.exchange_counts()
     ao, bo = orc.exchange_counts()
     assert np.array_equal(ag, ao) and np.array_equal(bg, bo), "exchange counters differ"
+    cg, lg = gpu.round_trips()
+    co, lo = orc.round_trips()
+    assert np.array_equal(cg, co) and np.array_equal(lg, lo), "round trips differ"

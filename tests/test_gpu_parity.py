@@ -139,3 +139,15 @@ def test_pipelined_walker_partial_batches():
                              exchange_interval=ex)
         run_both(gpu, orc, 4)
         gpu.close()
+
+
+def test_round_trips_on_a_converging_range():
+    """Restricted range [-400, 0] (bins narrower than the temperature): configurations cross all
+    four windows many times; round trips, exchanges and the walk agree bit for bit."""
+    gpu, orc = make_pair(group_size=1, L=4, J=(1.0, 0.5), e_min=-400.0, e_max=0.0, n_bins=60, n_windows=4,
+                         walkers_per_window=2, overlap=0.75, flatness=0.8, lnf_final=1e-6, seed=5,
+                         exchange_interval=200)
+    run_both(gpu, orc, 250)
+    c, _ = gpu.round_trips()
+    assert c.sum() > 5
+    gpu.close()

@@ -501,3 +501,45 @@ def test_accounting_before_first_reduction():
     assert np.all(w["stage"] == 0)
     assert np.all(w["H"].sum(1) == 2000) and np.all(w["steps"] == 2000)
     assert np.all(w["lng"].sum(1) == 2000.0)       # ln f = 1 added once per move
+
+
+def test_round_trips_two_windows_equal_accepted_exchanges():
+    """Two windows, one walker each: every accepted swap brings one configuration from the highest
+    window to the lowest, and both were seen at their extremes before, so the round trips of all
+    configurations add up to the accepted exchanges (Sec. 5, Fig. 1)."""
+    sim = o.OracleREWL(kind=o.BCC, L=4, J=(1.0, 0.5), e_min=-400.0, e_max=0.0, n_bins=60, n_windows=2,
+                       walkers_per_window=1, overlap=0.75, seed=3, exchange_interval=200)
+    sim.init_walkers()
+    sim.run_intervals(150)
+    counts, last = sim.round_trips()
+    _, acc = sim.exchange_counts()
+    assert acc[0] > 10 and counts.sum() == acc[0]
+    assert sorted(last.tolist()) == [0, 1]
+
+
+def test_round_trips_match_a_recount_from_the_replica_paths():
+    """Recount from the windows each configuration occupies after every exchange round (one
+    exchange round per interval), independently of the oracle's own counter."""
+    h, m = 4, 2
+    sim = o.OracleREWL(kind=o.BCC, L=4, J=(1.0, 0.5), e_min=-400.0, e_max=0.0, n_bins=60, n_windows=h,
+                       walkers_per_window=m, overlap=0.75, seed=5, exchange_interval=200)
+    sim.init_walkers()
+    S = h * m
+    paths = [np.arange(S)]                      # slot -> configuration before the first round
+    for _ in range(250):
+        sim.run_intervals(1)
+        paths.append(sim.walkers()["replica"].copy())
+    counts = np.zeros(S, dtype=np.int64)
+    last = np.full(S, -1)
+    for perm in paths:
+        window = np.empty(S, dtype=int)
+        window[perm] = np.arange(S) // m        # window of every configuration
+        for r in range(S):
+            if window[r] == 0:
+                counts[r] += last[r] == 1
+                last[r] = 0
+            elif window[r] == h - 1:
+                last[r] = 1
+    c, l = sim.round_trips()
+    assert counts.sum() > 5
+    assert np.array_equal(c, counts) and np.array_equal(l, last)
