@@ -48,6 +48,11 @@ enum {
 };
 
 enum {
+  REWL_ITERATION_WALKER = 0, /* each walker proceeds to its next iteration on its own (default) */
+  REWL_ITERATION_WINDOW = 1  /* the walkers of a window proceed together, ln g averaged */
+};
+
+enum {
   REWL_MODE_PRODUCTION = 0, /* FP32 spins and dE; ln g and energy in 64-bit fixed point */
   REWL_MODE_TRAJECTORY = 1  /* everything FP64; reproduces the FP64 reference walk bit for bit */
 };
@@ -93,7 +98,10 @@ typedef struct {
   int32_t recompute_every;       /* full energy recomputation every this many intervals; 0 =
                                     default (production 8: replaces the running energy;
                                     trajectory 1: drift diagnostic only) */
-  int32_t reserved;
+  int32_t iteration;             /* REWL_ITERATION_WALKER (0): every walker halves ln f on its own
+                                    flat histogram (Sec. 4.3, as written); REWL_ITERATION_WINDOW (1):
+                                    a window moves on when all its walkers are flat, after their
+                                    ln g are averaged bin by bin */
   double lnf_initial;            /* initial ln f; 0 = 1 (f0 = e, Sec. 4.2) */
   double timeout_s;              /* wall-clock cap for rewl_run_stage (0 = none) */
   void* cuda_stream;             /* cudaStream_t used for every launch (NULL = default stream) */

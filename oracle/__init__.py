@@ -26,7 +26,7 @@ class _Params(C.Structure):
         ("overlap", C.c_double), ("flatness", C.c_double), ("lnf_final", C.c_double),
         ("lnf_initial", C.c_double),
         ("seed", C.c_uint64), ("exchange_interval", C.c_int64), ("group_size", C.c_int32),
-        ("init_max_moves", C.c_int64),
+        ("init_max_moves", C.c_int64), ("iteration", C.c_int32),
     ]
 
 
@@ -184,7 +184,7 @@ class OracleREWL:
     def __init__(self, kind=BCC, L=4, J=(1.0, 0.5), n_shells=None, nbr=None, Jt=None,
                  e_min=math.nan, e_max=math.nan, n_bins=200, n_windows=4, walkers_per_window=2,
                  overlap=0.75, flatness=0.8, lnf_final=1e-3, lnf_initial=1.0, seed=1,
-                 exchange_interval=10000, group_size=1, init_max_moves=1 << 40):
+                 exchange_interval=10000, group_size=1, init_max_moves=1 << 40, iteration=0):
         p = _Params()
         p.kind = kind
         p.L = L
@@ -214,6 +214,7 @@ class OracleREWL:
         p.seed = seed
         p.exchange_interval = exchange_interval
         p.group_size = group_size
+        p.iteration = iteration
         p.init_max_moves = init_max_moves
         h = C.c_void_p()
         err = C.create_string_buffer(256)

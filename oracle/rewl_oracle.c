@@ -260,6 +260,9 @@ int ro_create(const ro_params* p, ro_sim** out, char* err, int errlen) {
     set_err(err, errlen, "group_size must be 1, 2, 4, 8, 16 or 32"); free(s); return -1;
   }
   s->G = G;
+  if (p->iteration != 0 && p->iteration != 1) {
+    set_err(err, errlen, "iteration must be 0 (per walker) or 1 (per window)"); free(s); return -1;
+  }
 
   /* lattice and neighbour table */
   if (p->kind == RO_BCC) {
@@ -669,7 +672,48 @@ int ro_exchange(ro_sim* s) {
 /* over all W bins of its window; then ln f -> ln f / 2 (f -> sqrt f) and H -> 0, ln g kept.     */
 /* Each walker proceeds independently (Sec. 4.3).                                              */
 /* ------------------------------------------------------------------------------------------- */
+static int walker_flat(const ro_sim* s, int slot) {
+  const uint32_t* H = s->H + (size_t)slot * s->W;
+  uint32_t mn = H[0];
+  uint64_t sum = 0;
+  for (int w = 0; w < s->W; ++w) {
+    if (H[w] < mn) mn = H[w];
+    sum += H[w];
+  }
+  double mean = (double)sum / (double)s->W;
+  return sum > 0 && (double)mn >= s->p.flatness * mean;
+}
+
+/* Window-synchronous reading (the walkers of a window move on together): when every walker of a
+   still-active window is flat, each bin's ln g becomes the mean over the window's walkers (summed
+   in walker order), then ln f halves and H clears for all of them. */
+static int flatness_by_window(ro_sim* s) {
+  int halved = 0;
+  const int m = s->m;
+  for (int k = 0; k < s->h; ++k) {
+    const int s0 = k * m;
+    if (!(s->lnf[s0] >= s->p.lnf_final)) continue;
+    int all = 1;
+    for (int a = 0; a < m && all; ++a) all = walker_flat(s, s0 + a);
+    if (!all) continue;
+    for (int w = 0; w < s->W; ++w) {
+      double t = 0.0;
+      for (int a = 0; a < m; ++a) t = t + s->lng[(size_t)(s0 + a) * s->W + w];
+      const double avg = t / (double)m;
+      for (int a = 0; a < m; ++a) s->lng[(size_t)(s0 + a) * s->W + w] = avg;
+    }
+    for (int a = 0; a < m; ++a) {
+      s->lnf[s0 + a] = s->lnf[s0 + a] * 0.5;
+      memset(s->H + (size_t)(s0 + a) * s->W, 0, sizeof(uint32_t) * (size_t)s->W);
+      s->stage[s0 + a] += 1;
+      ++halved;
+    }
+  }
+  return halved;
+}
+
 int ro_flatness(ro_sim* s) {
+  if (s->p.iteration == 1) return flatness_by_window(s);
   int halved = 0;
   for (int slot = 0; slot < s->S; ++slot) {
     if (!(s->lnf[slot] >= s->p.lnf_final)) continue;

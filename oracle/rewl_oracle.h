@@ -53,6 +53,9 @@ typedef struct {
   int64_t exchange_interval;   /* moves per walker between exchanges */
   int32_t group_size;          /* G: lanes per neighbour sum; fixes the summation order */
   int64_t init_max_moves;      /* cap on the moves that drive a walker into its window */
+  int32_t iteration;           /* 0: every walker halves ln f on its own flat histogram (Sec. 4.3,
+                                  literal); 1: a window halves when all its walkers are flat, after
+                                  averaging their ln g */
 } ro_params;
 
 /* --- building blocks (exposed so that tests can pin them one by one) --- */

@@ -23,6 +23,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librewl.so")
 
 BCC, CHAIN, TABLE = 0, 1, 2
+ITERATION_WALKER, ITERATION_WINDOW = 0, 1
 PRODUCTION, TRAJECTORY = 0, 1
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
 _STATUS = {0: "REWL_OK", 1: "REWL_EINVAL", 2: "REWL_ENOMEM", 3: "REWL_ECUDA", 4: "REWL_ETIMEOUT",
@@ -52,7 +53,7 @@ class Windows(C.Structure):
 class Config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("mode", C.c_int32), ("group_size", C.c_int32),
                 ("exchange_interval", C.c_int64), ("max_moves_per_stage", C.c_int64),
-                ("init_max_moves", C.c_int64), ("recompute_every", C.c_int32), ("reserved", C.c_int32),
+                ("init_max_moves", C.c_int64), ("recompute_every", C.c_int32), ("iteration", C.c_int32),
                 ("lnf_initial", C.c_double), ("timeout_s", C.c_double), ("cuda_stream", C.c_void_p)]
 
 
@@ -200,7 +201,7 @@ class REWL:
                  n_bins=200, n_windows=4, walkers_per_window=2, overlap=0.75, flatness=0.8,
                  lnf_final=1e-3, seed=1, mode=PRODUCTION, group_size=0, exchange_interval=10000,
                  max_moves_per_stage=0, init_max_moves=0, recompute_every=0, lnf_initial=0.0,
-                 timeout_s=0.0, stream=None):
+                 timeout_s=0.0, stream=None, iteration=0):
         lib = load_library()
         lat = Lattice()
         lat.kind = kind
@@ -228,6 +229,7 @@ class REWL:
         cfg.max_moves_per_stage = max_moves_per_stage
         cfg.init_max_moves = init_max_moves
         cfg.recompute_every = recompute_every
+        cfg.iteration = iteration
         cfg.lnf_initial = lnf_initial
         cfg.timeout_s = timeout_s
         cfg.cuda_stream = _stream_ptr(stream)

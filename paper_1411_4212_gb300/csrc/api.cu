@@ -27,6 +27,7 @@ struct rewl_handle {
   uint32_t key1 = 0;
   long long exchange_interval = 0, max_moves_per_stage = 0, init_cap = 0;
   int recompute_every = 1;
+  bool by_window = false;         // window-synchronous iteration (REWL_ITERATION_WINDOW)
   double timeout_s = 0;
   cudaStream_t stream = nullptr;
   std::vector<int32_t> starts;
@@ -296,6 +297,9 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   h->max_moves_per_stage = cfg->max_moves_per_stage;
   h->init_cap = cfg->init_max_moves > 0 ? cfg->init_max_moves : (1LL << 40);
   h->recompute_every = cfg->recompute_every > 0 ? cfg->recompute_every : (h->traj ? 1 : 8);
+  if (cfg->iteration != REWL_ITERATION_WALKER && cfg->iteration != REWL_ITERATION_WINDOW)
+    return bad("iteration must be REWL_ITERATION_WALKER or REWL_ITERATION_WINDOW");
+  h->by_window = cfg->iteration == REWL_ITERATION_WINDOW;
   h->timeout_s = cfg->timeout_s;
   h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
   h->ex = exp_coeffs();
@@ -639,6 +643,7 @@ static FlatnessArgs flatness_args(rewl_handle* h) {
   fa.flatness = h->flatness;
   fa.lnf_final = h->lnf_final;
   fa.traj = h->traj ? 1 : 0;
+  fa.by_window = h->by_window ? 1 : 0;
   return fa;
 }
 
@@ -726,6 +731,7 @@ static rewl_status enqueue_intervals(rewl_handle* h, int n) {
   fa.flatness = h->flatness;
   fa.lnf_final = h->lnf_final;
   fa.traj = ea.traj;
+  fa.by_window = h->by_window ? 1 : 0;
   for (int i = 0; i < n; ++i) {
     const bool recompute = ((h->intervals_done + 1) % h->recompute_every) == 0;
     const WalkerArgs a = walker_args(h, false, recompute, h->exchange_interval);

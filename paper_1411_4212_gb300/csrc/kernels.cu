@@ -125,7 +125,70 @@ cudaError_t launch_exchange_batch(const ExchangeArgs* jobs, int n_jobs, cudaStre
 // the W bins of its window (and sum H > 0); then ln f -> ln f / 2, H -> 0, stage += 1.
 // One warp per walker.
 // ------------------------------------------------------------------------------------------------
+// Flat histogram of one walker: min H >= p * (sum H / W) and sum H > 0 (every lane gets the answer).
+__device__ __forceinline__ bool walker_flat(const FlatnessArgs& a, const uint32_t* H) {
+  const int lane = threadIdx.x & 31;
+  const int W = a.win.W;
+  uint32_t mn = 0xffffffffu;
+  unsigned long long sum = 0;
+  for (int w = lane; w < W; w += 32) {
+    const uint32_t v = H[w];
+    mn = v < mn ? v : mn;
+    sum += v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t om = __shfl_xor_sync(kFullMask, mn, o);
+    mn = om < mn ? om : mn;
+    sum += __shfl_xor_sync(kFullMask, sum, o);
+  }
+  const double mean = __ddiv_rn(__ull2double_rn(sum), (double)W);
+  return sum > 0 && __uint2double_rn(mn) >= __dmul_rn(a.flatness, mean);
+}
+
+// Window-synchronous reading: when every walker of the (still active) window k is flat, each bin's
+// ln g becomes the mean over the window's walkers (summed in walker order, FP64 in trajectory mode;
+// 2^-40 fixed point in production, the sum divided by m with truncation), then ln f halves and H
+// clears for all of them.  One warp.
+__device__ __forceinline__ void flatness_window_warp(const FlatnessArgs& a, const int k) {
+  const int lane = threadIdx.x & 31;
+  const int W = a.win.W, m = a.win.m, s0 = k * m;
+  const bool active = a.traj ? a.st.lnf[s0] >= a.lnf_final : (double)a.st.lnf_fx[s0] * kLngUnit >= a.lnf_final;
+  if (!active) return;
+  for (int i = 0; i < m; ++i)
+    if (!walker_flat(a, a.st.H + (size_t)(s0 + i) * W)) return;
+  for (int w = lane; w < W; w += 32) {
+    if (a.traj) {
+      double t = 0.0;
+      for (int i = 0; i < m; ++i) t = __dadd_rn(t, a.st.lng[(size_t)(s0 + i) * W + w]);
+      const double avg = __ddiv_rn(t, (double)m);
+      for (int i = 0; i < m; ++i) a.st.lng[(size_t)(s0 + i) * W + w] = avg;
+    } else {
+      long long t = 0;
+      for (int i = 0; i < m; ++i) t += a.st.lng_fx[(size_t)(s0 + i) * W + w];
+      const long long avg = t / m;
+      for (int i = 0; i < m; ++i) a.st.lng_fx[(size_t)(s0 + i) * W + w] = avg;
+    }
+    for (int i = 0; i < m; ++i) a.st.H[(size_t)(s0 + i) * W + w] = 0u;
+  }
+  for (int i = lane; i < m; i += 32) {
+    const int slot = s0 + i;
+    if (a.traj) {
+      a.st.lnf[slot] = __dmul_rn(a.st.lnf[slot], 0.5);
+    } else {
+      const long long f = a.st.lnf_fx[slot] >> 1;
+      a.st.lnf_fx[slot] = f;
+      a.st.lnf[slot] = (double)f * kLngUnit;
+    }
+    a.st.stage[slot] += 1;
+  }
+}
+
 __device__ __forceinline__ void flatness_warp(const FlatnessArgs& a, const int slot) {
+  if (a.by_window) {
+    // the warp of the window's first walker does the window (m <= 32 walkers per window)
+    if (slot % a.win.m == 0) flatness_window_warp(a, slot / a.win.m);
+    return;
+  }
   const int lane = threadIdx.x;
   const int W = a.win.W;
   bool active;

@@ -53,6 +53,7 @@ struct FlatnessArgs {
   double flatness;
   double lnf_final;
   int traj;
+  int by_window;               // 1: the walkers of a window move on together (ln g averaged)
 };
 cudaError_t launch_flatness(const FlatnessArgs& a, int n_slots, cudaStream_t stream);
 cudaError_t launch_flatness_batch(const FlatnessArgs* jobs, const int2* items, int n_items, cudaStream_t stream);

@@ -41,7 +41,7 @@ BAD = [
     dict(e_min=0.0, e_max=-1.0), dict(e_min=float("inf"), e_max=0.0), dict(group_size=3), dict(overlap=0.0),
     dict(kind=rw.TABLE, nbr=[[0, 5]], Jt=[[1.0, 1.0]], e_min=-1.0, e_max=1.0),
     dict(kind=rw.TABLE, nbr=[[1, 0]], Jt=[[1.0, 1.0]]),
-    dict(kind=7),
+    dict(kind=7), dict(iteration=2),
 ]
 
 

@@ -151,3 +151,19 @@ def test_round_trips_on_a_converging_range():
     c, _ = gpu.round_trips()
     assert c.sum() > 5
     gpu.close()
+
+
+@pytest.mark.parametrize("m,intervals,stages", [(3, 900, 2), (2, 40, 1)])
+def test_window_synchronous_iteration(m, intervals, stages):
+    """The walkers of a window move on together (ln g averaged bin by bin, then ln f halved): bit for
+    bit against the oracle on a converging range (m = 3) and on the cfg1 geometry (m = 2)."""
+    if m == 3:
+        cfg = dict(L=4, J=(1.0, 0.5), e_min=-400.0, e_max=0.0, n_bins=60, n_windows=3, walkers_per_window=3,
+                   overlap=0.75, flatness=0.8, lnf_final=1e-3, seed=9, exchange_interval=300)
+    else:
+        cfg = dict(CFG1, exchange_interval=10000)
+    gpu, orc = make_pair(group_size=1, iteration=1, **cfg)
+    run_both(gpu, orc, intervals)
+    st = gpu.walkers()["stage"].reshape(-1, m)
+    assert st.max() >= stages and np.all(st == st[:, :1])
+    gpu.close()

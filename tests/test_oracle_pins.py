@@ -543,3 +543,49 @@ def test_round_trips_match_a_recount_from_the_replica_paths():
     c, l = sim.round_trips()
     assert counts.sum() > 5
     assert np.array_equal(c, counts) and np.array_equal(l, last)
+
+
+def _restricted(**kw):
+    cfg = dict(kind=o.BCC, L=4, J=(1.0, 0.5), e_min=-400.0, e_max=0.0, n_bins=60, n_windows=3, overlap=0.75,
+               exchange_interval=300, lnf_final=1e-3)
+    cfg.update(kw)
+    return o.OracleREWL(**cfg)
+
+
+def test_window_iteration_with_one_walker_is_the_walker_iteration():
+    a = _restricted(walkers_per_window=1, seed=7, iteration=0)
+    b = _restricted(walkers_per_window=1, seed=7, iteration=1)
+    for sim in (a, b):
+        sim.init_walkers()
+        sim.run_intervals(800)
+    wa, wb = a.walkers(), b.walkers()
+    assert wa["stage"].min() >= 3
+    for k in wa:
+        assert np.array_equal(wa[k], wb[k]), k
+
+
+def test_window_iteration_moves_the_walkers_of_a_window_together():
+    """After an interval in which a window moved on, its walkers hold one ln g (the average); at all
+    times they share ln f and the stage count."""
+    h, m = 3, 3
+    sim = _restricted(walkers_per_window=m, seed=9, iteration=1)
+    sim.init_walkers()
+    prev = sim.walkers()["stage"].copy()
+    moved = 0
+    for _ in range(900):
+        sim.run_intervals(1)
+        w = sim.walkers()
+        st = w["stage"].reshape(h, m)
+        lnf = w["lnf"].reshape(h, m)
+        assert np.all(st == st[:, :1]) and np.all(lnf == lnf[:, :1])
+        lng = w["lng"].reshape(h, m, -1)
+        for k in np.nonzero(st[:, 0] > prev.reshape(h, m)[:, 0])[0]:
+            assert all(np.array_equal(lng[k, 0], lng[k, a]) for a in range(1, m))
+            moved += 1
+        prev = w["stage"].copy()
+    assert moved >= 3
+
+
+def test_iteration_mode_is_validated():
+    with pytest.raises(ValueError):
+        _restricted(walkers_per_window=2, seed=1, iteration=2)
