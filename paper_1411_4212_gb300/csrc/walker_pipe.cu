@@ -191,9 +191,9 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
   p += sizeof(Real) * kMaxSlotsPerSite;
   Rec<kTraj>* rec = reinterpret_cast<Rec<kTraj>*>(p);
   p += sizeof(Rec<kTraj>) * 64;
-  int4* pk = reinterpret_cast<int4*>(p);          // production: {dq lo, dq hi, ccur, -} per move
+  int4* pk = reinterpret_cast<int4*>(p);          // production: {dq lo, dq hi, ccur, ln u} per move
   p += sizeof(int4) * 64;
-  uint32_t* fhist = reinterpret_cast<uint32_t*>(p);  // production: energy fraction before each move
+  uint32_t* fhist = reinterpret_cast<uint32_t*>(p);  // production: energy fraction before each move of a block
   p += sizeof(uint32_t) * 32;
   uint2* own = reinterpret_cast<uint2*>(p);
   p += sizeof(uint2) * ((size_t)omask + 1);
@@ -567,18 +567,23 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
     uint32_t acc_prev = 0, pub_prev = 0;
     int n_rec = 0;
     long long n_acc = 0;
-    // Two ways through a batch, with the same decisions: branch-free blocks of 8 moves with the
-    // rare events out of line (wide bins), or one move at a time (narrow bins, where most moves
-    // change bin).  A batch with many events sends the next one down the sequential path, a
-    // sequential batch with few sends it back.
-    bool sequential = false;
+    // Three ways through a batch, all with the same decisions; each batch takes the cheapest for
+    // the counts of the batch before it: n_rej moves that left the bin to a neighbour and were
+    // rejected, n_ev moves resolved out of line (accepted bin changes, jumps of two or more bins,
+    // corrections).
+    //   scan       -- one warp scan, one ballot round per event: few events (high-energy windows);
+    //   blocks     -- branch-free blocks of 8 moves absorb rejected exits: many of those, few others
+    //                 (low-energy windows);
+    //   sequential -- one move at a time: many full resolutions (bins as narrow as the temperature).
+    enum { kScan = 0, kBlocks = 1, kSequential = 2 };
+    int path = kBlocks;
     for (int b = 0; b < nb; ++b) {
       const int cur = b & 1;
       named_sync(kBarReady + cur);
       const int nvalid = bad ? 0 : (int)(moves - (long long)b * 32 < 32 ? moves - (long long)b * 32 : 32);
       int k_seg = 0;
       uint32_t acc_cur = 0, sup = 0;
-      int events = 0;
+      int n_rej = 0, n_ev = 0;
       Rec<false>* Rc = rec + cur * 32;
       const Rec<false>* Rp = rec + (cur ^ 1) * 32;
       // ---- parallel part: lane = move index ----
@@ -616,7 +621,8 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         __syncwarp();
       }
       const int my_lu = mine.lu;
-      // would a step to bcur + 1 / bcur - 1 be accepted at this move, given no change of bin since k_seg
+      // would a step to bcur + 1 / bcur - 1 be accepted at this move, given no change of bin since
+      // k_seg (lane = move; ln g at move k is lng_seg + (k - k_seg) ln f)
       auto pass_masks = [&](uint32_t& up, uint32_t& down) {
         const long long ln = lng_seg + (long long)(lane - k_seg) * lnf_eff;
         const long long du = ln - lng_p, dd = ln - lng_m;
@@ -627,10 +633,9 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         up = __ballot_sync(kFullMask, pu);
         down = __ballot_sync(kFullMask, pd);
       };
-      uint32_t up_mask = 0, down_mask = 0;
       // One move kk with increment dq (corrected first if it meets an accepted move of this batch):
       // Metropolis step on ln g, bin bookkeeping; every lane computes the same values.  Returns
-      // whether a bin change happened (the pass masks are then stale).
+      // whether the walker changed bin.
       auto resolve = [&](const int kk, long long dq, const uint32_t ccur_w, const int lu) -> bool {
         const uint32_t m = ccur_w & acc_cur;
         uint32_t same = 0u;
@@ -649,7 +654,6 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
           }
           __syncwarp();
           ++n_rec;
-          ++events;
         }
         const long long Ep = Efx + dq;
         const int db = fx_bin(Ep) - bcur;
@@ -664,6 +668,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
             const long long d = lng_now - lngp;
             const int e20 = d < -(1LL << 51) ? (int)0x80000000 : (int)(d >> 20);
             acc = d >= 0 || lu < e20;
+            moved = acc;
             if (acc) {
               // leave bcur: write it back, shift the neighbour cache, start a new segment
               lng_s[bcur - wlo] = (Lng)lng_now;
@@ -676,7 +681,6 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
               bcur = bp;
               if (db != -1) lng_p = bcur + 1 < wlo + W ? (long long)lng_s[bcur + 1 - wlo] : 0;
               if (db != 1) lng_m = bcur - 1 >= wlo ? (long long)lng_s[bcur - 1 - wlo] : 0;
-              moved = true;
             }
           }
         }
@@ -685,13 +689,80 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
           acc_cur |= 1u << kk;
           sup |= same;   // earlier accepted moves on this site are no longer the site's spin
         }
-        // the events that leave a block of the branch-free path: corrections (counted above),
-        // accepted bin changes, jumps of two or more bins
-        events += (moved || db > 1 || db < -1) ? 1 : 0;
+        const bool neighbour_reject = !acc && (db == 1 || db == -1) && !m;
+        n_rej += neighbour_reject ? 1 : 0;
+        n_ev += (db != 0 && !neighbour_reject) || m ? 1 : 0;
         return moved;
       };
+      // ---- sequential part as a scan ----
+      // A move that stays in the current bin is accepted (ln g ratio 1), so between events the
+      // energy is a running sum: with P_k the inclusive prefix sum of the batch's increments and
+      // segment base B (fraction before move s minus the prefix before s), move k >= s lands at
+      // fraction B + P_k.  The first move that leaves [0, 2^32) -- or meets an accepted move of this
+      // batch -- ends the segment: the moves before it stand.  A step to a neighbouring bin whose
+      // pass bit is clear is rejected on the spot (the base drops its increment); anything else is
+      // resolved on its own.  One scan per batch, one round of ballots per such move.
       const int4* P4 = pk + cur * 32;
-      if (sequential) {
+      uint32_t up_mask = 0, down_mask = 0;
+      if (path == kScan && nvalid > 0) {
+        const int4 wk = P4[lane];
+        const long long dqk = lane < nvalid ? (long long)(((unsigned long long)(uint32_t)wk.y << 32) | (uint32_t)wk.x)
+                                            : 0LL;
+        long long P = dqk;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long t = __shfl_up_sync(kFullMask, P, o);
+          if (lane >= o) P += t;
+        }
+        const uint32_t cck = (uint32_t)wk.z;
+        const uint32_t below = (1u << lane) - 1u;          // moves before this one
+        const uint32_t upto = nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u);
+        pass_masks(up_mask, down_mask);
+        long long B = (long long)(uint32_t)Efx;
+        int s0 = 0;
+        while (true) {
+          const uint32_t from_s = ~((1u << s0) - 1u);      // moves s0 .. 31
+          const long long pos = B + P;
+          const bool live = lane >= s0 && lane < nvalid;
+          const uint32_t outs = __ballot_sync(kFullMask, live && (unsigned long long)pos >= (1ull << 32));
+          const uint32_t needs = __ballot_sync(kFullMask, live && (cck & (acc_cur | (below & from_s))) != 0u);
+          const uint32_t ev = outs | needs;
+          if (ev == 0u) {
+            // the rest of the batch stays in the bin
+            acc_cur |= upto & from_s;
+            const long long Pl = __shfl_sync(kFullMask, P, nvalid - 1);
+            Efx = ((long long)bcur << 32) | (long long)(uint32_t)(B + Pl);
+            break;
+          }
+          const int e = __ffs(ev) - 1;
+          const uint32_t bit = 1u << e;
+          acc_cur |= (bit - 1u) & from_s;
+          const long long pe = __shfl_sync(kFullMask, pos, e);
+          const long long de = __shfl_sync(kFullMask, dqk, e);
+          if (!(needs & bit)) {
+            // leaves the bin: one bin up or down with the pass bit clear is rejected here
+            const bool one_up = pe >= (1LL << 32) && pe < (2LL << 32);
+            const bool one_down = pe < 0 && pe >= -(1LL << 32);
+            if ((one_up && !(up_mask & bit)) || (one_down && !(down_mask & bit))) {
+              ++n_rej;
+              B -= de;
+              s0 = e + 1;
+              if (s0 >= nvalid) {
+                Efx = ((long long)bcur << 32) | (long long)(uint32_t)(pe - de);
+                break;
+              }
+              continue;
+            }
+          }
+          Efx = ((long long)bcur << 32) | (long long)(uint32_t)(pe - de);
+          const int4 we = P4[e];
+          const long long dq = (long long)(((unsigned long long)(uint32_t)we.y << 32) | (uint32_t)we.x);
+          if (resolve(e, dq, (uint32_t)we.z, we.w)) pass_masks(up_mask, down_mask);
+          s0 = e + 1;
+          if (s0 >= nvalid) break;
+          B = (long long)(uint32_t)Efx - (pe - B);
+        }
+      } else if (path == kSequential) {
         // ---- sequential part, one move at a time ----
         int4 w = P4[0];
         for (int kk = 0; kk < nvalid; ++kk) {
@@ -700,7 +771,6 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
           resolve(kk, dq, (uint32_t)w.z, w.w);
           w = wn;
         }
-        sequential = events >= 4;
       } else {
         // ---- sequential part, in branch-free blocks of 8 moves ----
         // Within a bin the state is frac = Efx - (bcur << 32) in [0, 2^32).  A move in the same bin
@@ -711,10 +781,9 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         pass_masks(up_mask, down_mask);
         uint32_t frac = (uint32_t)Efx;
         int k = 0;
-        int n_out = 0;
         while (k < nvalid) {
           const uint32_t acc0 = acc_cur;
-          uint32_t exc = 0;
+          uint32_t exc = 0, outb = 0;
           int4 q[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) q[u] = P4[(k + u) & 31];
@@ -734,6 +803,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
             const uint32_t stay = ~nz & vmask;
             frac = (t_lo & stay) | (frac & ~stay);
             acc_cur |= bit & stay;
+            outb |= bit & nz;
             const uint32_t up = (uint32_t)(((th - 1) | (1 - th)) >> 31);       // all ones iff th != 1
             const uint32_t dn = (uint32_t)(((th + 1) | (-1 - th)) >> 31);      // all ones iff th != -1
             const uint32_t far = nz & up & dn;                                  // |th| >= 2
@@ -741,9 +811,11 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
             exc |= bit & (((~up) & up_mask) | ((~dn) & down_mask) | far | (need ? 0xffffffffu : 0u));
           }
           if (exc == 0u) {
+            n_rej += __popc(outb);
             k += 8;
             continue;
           }
+          n_rej += __popc(outb & ((exc & (0u - exc)) - 1u));
           // first exceptional move: the block's moves before it stand; restore the state there
           const int kx = __ffs(exc) - 1;
           __syncwarp();
@@ -754,12 +826,11 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
           const long long dq = (long long)(((unsigned long long)(uint32_t)wx.y << 32) | (uint32_t)wx.x);
           if (resolve(kx, dq, (uint32_t)wx.z, wx.w)) pass_masks(up_mask, down_mask);
           frac = (uint32_t)Efx;
-          ++n_out;
           k = kx + 1;
         }
         Efx = ((long long)bcur << 32) | frac;
-        sequential = n_out >= 6;
       }
+      path = (n_rej + n_ev <= 6) ? kScan : (n_ev >= 6 ? kSequential : kBlocks);
       // the batch's moves at the current bin
       lng_seg += (long long)(nvalid - k_seg) * lnf_eff;
       h_seg += hinc * (uint32_t)(nvalid - k_seg);
