@@ -830,7 +830,9 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         }
         Efx = ((long long)bcur << 32) | frac;
       }
-      path = (n_rej + n_ev <= 6) ? kScan : (n_ev >= 6 ? kSequential : kBlocks);
+      // measured: blocks cost about 90 cycles per move whatever the rejected exits; the scan about
+      // 200 per batch plus 260 per event, so it wins below about 10 events per batch
+      path = (n_rej + n_ev <= 10) ? kScan : (n_ev >= 6 ? kSequential : kBlocks);
       // the batch's moves at the current bin
       lng_seg += (long long)(nvalid - k_seg) * lnf_eff;
       h_seg += hinc * (uint32_t)(nvalid - k_seg);
