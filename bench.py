@@ -34,6 +34,10 @@ WORKLOAD = dict(L=16, J=(1.0, 0.5), n_bins=2000, n_windows=16, walkers_per_windo
                 flatness=0.8, lnf_final=1e-8, exchange_interval=10000)
 WORKLOAD_NAME = ("REWL bcc L=16 (8192 spins) J1=1 J2=0.5, [E_gs,0] 2000 bins, 16 windows x 4 walkers, "
                  "75% overlap, exchange every 1e4 moves")
+LARGE = dict(L=32, J=(1.0, 0.6, -0.05, -0.1), n_bins=8000, n_windows=64, walkers_per_window=8, overlap=0.75,
+             flatness=0.8, lnf_final=1e-8, exchange_interval=10000)
+LARGE_NAME = ("REWL bcc L=32 (65536 spins) J=(1,0.6,-0.05,-0.1) (50 neighbours), [E_gs,0] 8000 bins, "
+              "64 windows x 8 walkers, 75% overlap, exchange every 1e4 moves")
 METRIC = "spin-move attempts/s"
 UNIT = "moves/s"
 
@@ -49,8 +53,10 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--jobs-per-size", type=int, default=16,
                    help="batch64: jobs per lattice size (16 gives the 64-job workload; smaller for profiling)")
-    p.add_argument("--workload", default="single", choices=["single", "batch64", "warmstart", "weak-scaling"],
-                   help="single: one job, bcc L=16 (the headline line); batch64: 64 jobs of bcc L=8..20 "
+    p.add_argument("--workload", default="single",
+                   choices=["single", "large", "batch64", "warmstart", "weak-scaling"],
+                   help="single: one job, bcc L=16 (the headline line); large: one job, bcc L=32 with four "
+                        "shells, 64 windows x 8 walkers; batch64: 64 jobs of bcc L=8..20 "
                         "in one persistent launch; warmstart: learned warm start versus plain REWL; "
                         "weak-scaling: moves to finish the first WL iteration versus L")
     return p.parse_args()
@@ -425,10 +431,11 @@ def main():
     stream = torch.cuda.current_stream()
     I = args.intervals
 
-    sim = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, seed=replica_seed(rank), stream=stream, **WORKLOAD)
+    workload, workload_name = (LARGE, LARGE_NAME) if args.workload == "large" else (WORKLOAD, WORKLOAD_NAME)
+    sim = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, seed=replica_seed(rank), stream=stream, **workload)
     sim.init_walkers()
     S, B = sim.n_slots, sim.B
-    moves_per_step = S * WORKLOAD["exchange_interval"] * I
+    moves_per_step = S * workload["exchange_interval"] * I
     out = torch.zeros(B, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -478,12 +485,14 @@ def main():
     z = sim.z
     bytes_per_move = 12 * z + 12 + 2 * 8 + 8 + 4 + 12 * acc_rate
     walk_avg_ms = statistics.mean(walk_ms)
-    achieved = bytes_per_move * S * WORKLOAD["exchange_interval"] / (walk_avg_ms * 1e-3)
+    achieved = bytes_per_move * S * workload["exchange_interval"] / (walk_avg_ms * 1e-3)
     smem_peak, _ = rw.measure_smem_bandwidth(stream)
     walker_share = sum(walk_ms) / sum(step_ms)
     pipelined = bool(sim.info()["pipelined"])
-    kernel = "walker_pipe_kernel<false,true,%d>" % len(WORKLOAD["J"]) if pipelined else "walker_kernel<false,true>"
-    traffic = profiled_traffic(kernel, S * WORKLOAD["exchange_interval"])
+    in_smem = "true" if sim.info()["lattice_in_shared"] else "false"
+    kernel = (f"walker_pipe_kernel<false,{in_smem},{len(workload['J'])}>" if pipelined
+              else f"walker_kernel<false,{in_smem}>")
+    traffic = profiled_traffic(kernel, S * workload["exchange_interval"])
 
     # end to end through the public API with host buffers: ln g in (warm start), merged ln g out
     lng_in = np.zeros(B)
@@ -504,7 +513,7 @@ def main():
     e2e_value = moves_per_step * len(e2e_ms) * world / (e2e_total * 1e-3)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and world >= 1 and args.gpus == 1:
+    if rank == 0 and not args.no_cpu_baseline and args.gpus == 1 and args.workload == "single":
         cpu = cpu_baseline(args.cpu_seconds)
 
     if rank == 0:
@@ -513,7 +522,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp32 spins/dE + int64 fixed-point ln g/energy",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "intervals_per_step": I,
+            "config": {"workload": workload_name, "intervals_per_step": I,
                        "moves_per_step": moves_per_step * world, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"{world} independent replica(s), one per GPU",
                        "group_size": sim.info()["group_size"], "accept_rate": acc_rate,
@@ -523,7 +532,7 @@ def main():
                          "kernel": kernel, "bytes_per_move": bytes_per_move,
                          "walker_ms_per_launch": walk_avg_ms, "walker_share_of_step": walker_share,
                          "cycles_per_move_per_walker": walk_avg_ms * 1e-3 * (clk.get("sm_mhz") or 0) * 1e6
-                                                       / WORKLOAD["exchange_interval"],
+                                                       / workload["exchange_interval"],
                          "sms_used": min(S, torch.cuda.get_device_properties(dev).multi_processor_count),
                          "peak_source": "measured live: conflict-free 16-byte shared-memory loads on every SM"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
