@@ -385,14 +385,18 @@ def run_warmstart(args):
     ok, res, wall = warmstart.warm_vs_cold(net, 8, held, lnf_final=1e-5, replicas=2, separate=True)
     cold = float(np.mean([m for r in res for m in r["cold_moves"]]))
     warm = float(np.mean([m for r in res for m in r["warm_moves"]]))
+    # Monte Carlo time: trial moves per walker until a job has converged, averaged over the jobs.
+    # The wall time of each group is that of its slowest job (all run in one batch), so it is
+    # reported beside it but is not the comparison.
     line = {
-        "metric": "time to converged ln g, warm start / plain", "value": wall[1] / wall[0], "unit": "ratio",
-        "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+        "metric": "Monte Carlo time (moves per walker) to converged ln g, warm start / plain", "value": warm / cold,
+        "unit": "ratio", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
         "config": {"workload": "warm start: corpus 192 runs bcc L=4,5,6 (ln f->1e-4), evaluation 4 held-out "
                                "coupling sets at bcc L=8, 16 windows x 2 walkers, ln f->1e-5, range [0.6 E_gs, 0], "
                                "one bin per spin, ln f0 = 2^-7 (warm) vs 1 (plain)",
                    "converged": bool(ok and meta["converged"])},
-        "wall_s": {"plain": wall[0], "warm": wall[1], "corpus": t1 - t0, "training": t2 - t1},
+        "wall_s": {"plain": wall[0], "warm": wall[1], "ratio": wall[1] / wall[0], "corpus": t1 - t0,
+                   "training": t2 - t1, "note": "each group's slowest job of 8"},
         "moves_per_walker": {"plain": cold, "warm": warm, "ratio": warm / cold},
         "rms": {"prediction": float(np.mean([r["prediction_rms"] for r in res])),
                 "plain_vs_plain": float(np.mean([v for r in res for v in r["cold_rms"]])),
