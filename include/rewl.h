@@ -293,12 +293,15 @@ typedef struct {
   int workers_per_block;     /* walker pairs (64 threads each) per CTA, 1..3 */
   int smem_lattice_max_n;    /* jobs with n_spins <= this keep the lattice in shared memory (if it
                                 fits the arena); 0 = none; the others read it from global memory */
+  int owner_entries_max;     /* jobs with the lattice in global memory: conflict-table entries at most
+                                (a power of two, 256..8192; 0 = 8192).  Fewer entries fit more walker
+                                pairs per SM; sites sharing an entry cost extra corrections */
 } rewl_batch_tuning;
 
 typedef struct {
   int n_jobs, n_items;       /* jobs, walker slots over all jobs */
   int n_active_jobs;         /* jobs in the work list (see rewl_batch_run_to_convergence) */
-  int workers_per_block, smem_lattice_max_n;
+  int workers_per_block, smem_lattice_max_n, owner_entries_max;
   int grid, blocks_per_sm;   /* persistent launch: CTAs, resident CTAs per SM */
   int n_smem_lattice_jobs;   /* jobs whose lattice sits in shared memory */
   int64_t arena_bytes;       /* shared memory per walker pair */
@@ -317,7 +320,8 @@ rewl_status rewl_batch_create(rewl_handle* const* jobs, int n_jobs, void* cuda_s
 rewl_status rewl_batch_set_tuning(rewl_batch* b, const rewl_batch_tuning* t);
 
 /* Autotuner: time one walker launch of trial_moves moves per walker (> 0) for every candidate
- * (workers_per_block 1..3 x every lattice-size threshold of the batch's jobs), keep the fastest.
+ * (workers_per_block 1..3 x every lattice-size threshold of the batch's jobs x conflict tables of
+ * 8192 down to 512 entries), keep the fastest.
  * The timed moves are ordinary Wang-Landau moves of the jobs: the walkers advance by them.
  * chosen (host, may be NULL) receives the tuning; ms_out (host, may be NULL) its trial time. */
 rewl_status rewl_batch_autotune(rewl_batch* b, int64_t trial_moves, rewl_batch_tuning* chosen, double* ms_out);

@@ -81,12 +81,14 @@ class Info(C.Structure):
 
 
 class BatchTuning(C.Structure):
-    _fields_ = [("workers_per_block", C.c_int32), ("smem_lattice_max_n", C.c_int32)]
+    _fields_ = [("workers_per_block", C.c_int32), ("smem_lattice_max_n", C.c_int32),
+                ("owner_entries_max", C.c_int32)]
 
 
 class BatchInfo(C.Structure):
     _fields_ = [("n_jobs", C.c_int32), ("n_items", C.c_int32), ("n_active_jobs", C.c_int32),
-                ("workers_per_block", C.c_int32), ("smem_lattice_max_n", C.c_int32), ("grid", C.c_int32),
+                ("workers_per_block", C.c_int32), ("smem_lattice_max_n", C.c_int32),
+                ("owner_entries_max", C.c_int32), ("grid", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("n_smem_lattice_jobs", C.c_int32), ("arena_bytes", C.c_int64),
                 ("intervals_done", C.c_int64), ("graphs_built", C.c_int32)]
 
@@ -407,8 +409,8 @@ class Batch:
     def __exit__(self, *exc):
         self.close()
 
-    def set_tuning(self, workers_per_block, smem_lattice_max_n):
-        t = BatchTuning(int(workers_per_block), int(smem_lattice_max_n))
+    def set_tuning(self, workers_per_block, smem_lattice_max_n, owner_entries_max=0):
+        t = BatchTuning(int(workers_per_block), int(smem_lattice_max_n), int(owner_entries_max))
         _check(self._lib.rewl_batch_set_tuning(self._b, C.byref(t)))
 
     def autotune(self, trial_moves=2000):
@@ -416,7 +418,7 @@ class Batch:
         ms = C.c_double()
         _check(self._lib.rewl_batch_autotune(self._b, int(trial_moves), C.byref(t), C.byref(ms)))
         return {"workers_per_block": t.workers_per_block, "smem_lattice_max_n": t.smem_lattice_max_n,
-                "trial_ms": ms.value}
+                "owner_entries_max": t.owner_entries_max, "trial_ms": ms.value}
 
     def run_intervals(self, n):
         _check(self._lib.rewl_batch_run_intervals(self._b, int(n)))

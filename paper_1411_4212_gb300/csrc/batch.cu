@@ -25,7 +25,7 @@ struct rewl_batch {
   int max_smem = 0, n_sms = 0;
 
   // tuning
-  int workers = 0, smem_max_n = 0;
+  int workers = 0, smem_max_n = 0, own_cap = 8192;
   size_t arena = 0;
   int grid = 0, bps = 0, n_smem_jobs = 0;
   std::vector<WalkerArgs> wargs;
@@ -84,24 +84,28 @@ void drop_graphs(rewl_batch* b) {
   }
 }
 
-int own_full_entries(int N) {
+// Conflict-table entries wanted: one per site up to 8192 (lattices in shared memory), at most
+// own_cap for lattices in global memory.
+int own_full_entries(int N, bool smem_lattice, int own_cap) {
   int e = 256;
-  while (e < N && e < 8192) e *= 2;
+  while (e < N && e < (smem_lattice ? 8192 : own_cap)) e *= 2;
   return e;
 }
 
-// Largest owner table (power of two, 256 .. own_full_entries(N)) that fits `cap` bytes; 0 if none.
-int fit_owner(bool traj, bool smem_lattice, int N, int W, size_t cap) {
-  for (int e = own_full_entries(N); e >= 256; e /= 2)
+// Largest owner table (power of two, 256 .. own_full_entries) that fits `cap` bytes; 0 if none.
+int fit_owner(bool traj, bool smem_lattice, int N, int W, size_t cap, int own_cap) {
+  for (int e = own_full_entries(N, smem_lattice, own_cap); e >= 256; e /= 2)
     if (walker_pipe_smem_bytes(traj, smem_lattice, N, W, e) <= cap) return e;
   return 0;
 }
 
 // Walker arguments, arena and launch shape for `workers` pairs per CTA and lattices with at most
 // smem_max_n spins in shared memory.
-rewl_status apply_tuning(rewl_batch* b, int workers, int smem_max_n) {
+rewl_status apply_tuning(rewl_batch* b, int workers, int smem_max_n, int own_cap) {
   if (workers < 1 || workers > kBatchMaxWorkers) return bfail(b, REWL_EINVAL, "workers_per_block must be 1..3");
   if (smem_max_n < 0) return bfail(b, REWL_EINVAL, "smem_lattice_max_n must be >= 0");
+  if (own_cap < 256 || own_cap > 8192 || (own_cap & (own_cap - 1)) != 0)
+    return bfail(b, REWL_EINVAL, "owner_entries_max must be a power of two in 256..8192");
   const size_t usable = (size_t)b->max_smem - 1024;   // static shared memory of the kernel and slack
   const size_t cap = (usable / (size_t)workers) & ~(size_t)15;
   const int n = (int)b->jobs.size();
@@ -109,12 +113,12 @@ rewl_status apply_tuning(rewl_batch* b, int workers, int smem_max_n) {
   size_t arena = 0;
   for (int j = 0; j < n; ++j) {
     const JobView& v = b->view[j];
-    bool s = v.N <= smem_max_n && fit_owner(b->traj, true, v.N, v.W, cap) > 0;
-    if (!s && fit_owner(b->traj, false, v.N, v.W, cap) == 0)
+    bool s = v.N <= smem_max_n && fit_owner(b->traj, true, v.N, v.W, cap, own_cap) > 0;
+    if (!s && fit_owner(b->traj, false, v.N, v.W, cap, own_cap) == 0)
       return bfail(b, REWL_EINVAL, "window tables of job " + std::to_string(j) + " do not fit the arena");
     in_smem[j] = s;
     // the smallest arena that still holds this job with its full owner table, else the cap
-    const int e = fit_owner(b->traj, s, v.N, v.W, cap);
+    const int e = fit_owner(b->traj, s, v.N, v.W, cap, own_cap);
     arena = std::max(arena, walker_pipe_smem_bytes(b->traj, s, v.N, v.W, e));
   }
   arena = (arena + 15) & ~(size_t)15;
@@ -123,6 +127,7 @@ rewl_status apply_tuning(rewl_batch* b, int workers, int smem_max_n) {
   if (bps < 1) return bfail(b, REWL_EINVAL, "batched walker does not fit on an SM with this tuning");
   b->workers = workers;
   b->smem_max_n = smem_max_n;
+  b->own_cap = own_cap;
   b->arena = arena;
   b->bps = bps;
   b->n_smem_jobs = 0;
@@ -130,7 +135,7 @@ rewl_status apply_tuning(rewl_batch* b, int workers, int smem_max_n) {
     const JobView& v = b->view[j];
     WalkerArgs& a = b->wargs[j];
     a = job_walker_args(b->jobs[j], b->moves, 0);
-    const int e = fit_owner(b->traj, in_smem[j] != 0, v.N, v.W, arena);
+    const int e = fit_owner(b->traj, in_smem[j] != 0, v.N, v.W, arena, own_cap);
     a.own_mask = e - 1;
     a.smem_lattice = in_smem[j];
     b->n_smem_jobs += in_smem[j];
@@ -344,7 +349,7 @@ extern "C" rewl_status rewl_batch_create(rewl_handle* const* jobs, int n_jobs, v
   // the batch's stream starts after the jobs' pending work (initial drive included)
   s = order_after_jobs(b);
   if (s == REWL_OK) s = build_work_list(b);
-  if (s == REWL_OK) s = apply_tuning(b, 2, 1 << 30);
+  if (s == REWL_OK) s = apply_tuning(b, 2, 1 << 30, 8192);
   if (s == REWL_OK) {
     const cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) s = bfail(b, REWL_ECUDA, std::string("set-up: ") + cudaGetErrorString(e));
@@ -363,11 +368,12 @@ extern "C" rewl_status rewl_batch_set_tuning(rewl_batch* b, const rewl_batch_tun
   rewl_status s = check_batch(b);
   if (s != REWL_OK) return s;
   if (!t) return bfail(b, REWL_EINVAL, "NULL tuning");
-  const int w0 = b->workers, n0 = b->smem_max_n;
-  s = apply_tuning(b, t->workers_per_block, t->smem_lattice_max_n);
+  const int w0 = b->workers, n0 = b->smem_max_n, c0 = b->own_cap;
+  s = apply_tuning(b, t->workers_per_block, t->smem_lattice_max_n,
+                   t->owner_entries_max == 0 ? 8192 : t->owner_entries_max);
   if (s == REWL_EINVAL && w0 > 0) {
     const std::string msg = rewl_last_error(nullptr);
-    apply_tuning(b, w0, n0);   // keep the previous, valid tuning
+    apply_tuning(b, w0, n0, c0);   // keep the previous, valid tuning
     set_handleless_error(msg);
   }
   return s;
@@ -389,10 +395,17 @@ extern "C" rewl_status rewl_batch_autotune(rewl_batch* b, int64_t trial_moves, r
   BCUDA(b, cudaEventCreate(&e0));
   BCUDA(b, cudaEventCreate(&e1));
   double best = -1.0;
-  int best_w = b->workers, best_n = b->smem_max_n;
+  int best_w = b->workers, best_n = b->smem_max_n, best_c = b->own_cap;
+  for (int own_cap : {8192, 4096, 2048, 1024, 512})
   for (int w = 1; w <= kBatchMaxWorkers; ++w) {
     for (int thr : thresholds) {
-      if (apply_tuning(b, w, thr) != REWL_OK) continue;   // does not fit: not a candidate
+      if (apply_tuning(b, w, thr, own_cap) != REWL_OK) continue;   // does not fit: not a candidate
+      if (own_cap < 8192) {   // a smaller cap is a new candidate only if it shrinks some job's table
+        bool shrinks = false;
+        for (int j : b->active_ids)
+          shrinks = shrinks || (!b->wargs[j].smem_lattice && b->view[j].N > own_cap);
+        if (!shrinks) continue;
+      }
       cudaError_t e = cudaEventRecord(e0, b->stream);
       if (e == cudaSuccess) e = launch_walkers_batch(walker_launch(b, trial_moves, 0), b->stream);
       if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
@@ -408,18 +421,20 @@ extern "C" rewl_status rewl_batch_autotune(rewl_batch* b, int64_t trial_moves, r
         best = ms;
         best_w = w;
         best_n = thr;
+        best_c = own_cap;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  s = apply_tuning(b, best_w, best_n);
+  s = apply_tuning(b, best_w, best_n, best_c);
   if (s != REWL_OK) return s;
   s = order_jobs_after(b);
   if (s != REWL_OK) return s;
   if (chosen) {
     chosen->workers_per_block = best_w;
     chosen->smem_lattice_max_n = best_n;
+    chosen->owner_entries_max = best_c;
   }
   if (ms_out) *ms_out = best;
   return REWL_OK;
@@ -485,6 +500,7 @@ extern "C" rewl_status rewl_batch_get_info(const rewl_batch* b, rewl_batch_info*
   out->n_active_jobs = (int)b->active_ids.size();
   out->workers_per_block = b->workers;
   out->smem_lattice_max_n = b->smem_max_n;
+  out->owner_entries_max = b->own_cap;
   out->grid = b->grid;
   out->blocks_per_sm = b->bps;
   out->n_smem_lattice_jobs = b->n_smem_jobs;

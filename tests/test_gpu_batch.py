@@ -35,15 +35,18 @@ def _traj_jobs(specs, recompute_every=0):
     return gpus, orcs
 
 
-@pytest.mark.parametrize("workers,smem_max_n", [(1, 0), (2, 300), (3, 1 << 30)])
-def test_batch_trajectory_matches_oracle(workers, smem_max_n):
+# (pairs per CTA, largest lattice kept in shared memory, conflict-table cap for global lattices):
+# a 256-entry cap makes sites of the L=5 and L=6 lattices share entries
+@pytest.mark.parametrize("workers,smem_max_n,own_cap", [(1, 0, 0), (1, 0, 256), (2, 300, 0), (3, 1 << 30, 0)])
+def test_batch_trajectory_matches_oracle(workers, smem_max_n, own_cap):
     gpus, orcs = _traj_jobs(JOBS)
     for o in orcs:
         o.init_walkers()
     with rw.Batch(gpus) as b:
-        b.set_tuning(workers, smem_max_n)
+        b.set_tuning(workers, smem_max_n, own_cap)
         info = b.info()
         assert info["workers_per_block"] == workers and info["n_items"] == sum(g.n_slots for g in gpus)
+        assert info["owner_entries_max"] == (own_cap or 8192)
         n_smem = sum(1 for g in gpus if g.N <= smem_max_n)
         assert info["n_smem_lattice_jobs"] == n_smem
         b.run_intervals(5)
@@ -132,8 +135,10 @@ def test_batch_rejects_mixed_jobs():
             rw.Batch(list(pair))
         assert e.value.status == rw.EINVAL
     with rw.Batch([a]) as bt:
-        with pytest.raises(rw.RewlError):
-            bt.set_tuning(4, 0)
-        assert bt.info()["workers_per_block"] == 2   # the previous tuning stays
+        for bad in ((4, 0, 0), (2, 0, 300), (2, 0, 128), (2, 0, 16384)):
+            with pytest.raises(rw.RewlError):
+                bt.set_tuning(*bad)
+        info = bt.info()   # the previous tuning stays
+        assert info["workers_per_block"] == 2 and info["owner_entries_max"] == 8192
     for h in (a, b, c):
         h.close()
