@@ -474,6 +474,8 @@ def main():
     workload, workload_name = (LARGE, LARGE_NAME) if args.workload == "large" else (WORKLOAD, WORKLOAD_NAME)
     sim = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, seed=replica_seed(rank), stream=stream, **workload)
     sim.init_walkers()
+    # lattices in global memory: the conflict-table size is timed before the warm-up (ordinary moves)
+    tune = sim.autotune(trial_moves=2000) if not sim.info()["lattice_in_shared"] else None
     S, B = sim.n_slots, sim.B
     moves_per_step = S * workload["exchange_interval"] * I
     out = torch.zeros(B, dtype=torch.float64, device=dev)
@@ -566,7 +568,8 @@ def main():
                        "moves_per_step": moves_per_step * world, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"{world} independent replica(s), one per GPU",
                        "group_size": sim.info()["group_size"], "accept_rate": acc_rate,
-                       "recompute_rate": rec_rate},
+                       "recompute_rate": rec_rate, "conflict_entries": sim.info()["conflict_entries"],
+                       "autotune": tune},
             "roofline": {"bound": "smem", "achieved": achieved / 1e9, "peak": smem_peak / 1e9, "unit": "GB/s",
                          "frac": achieved / smem_peak, "traffic": traffic,
                          "kernel": kernel, "bytes_per_move": bytes_per_move,

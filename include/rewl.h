@@ -132,6 +132,8 @@ typedef struct {
   size_t shared_bytes_per_walker;
   int32_t lattice_in_shared;   /* 1 when each walker's spins live in shared memory */
   int32_t pipelined;           /* 1 when the Wang-Landau moves run on the warp-specialised walker */
+  int32_t conflict_entries;    /* pipelined walker: entries of its per-walker conflict table (sites
+                                  map to entry site mod entries); 0 otherwise */
 } rewl_info;
 
 typedef struct {
@@ -176,6 +178,17 @@ rewl_status rewl_run_stage(rewl_handle* h, rewl_stage_stats* stats);
  * rewl_flatness applies the flatness test and ln f -> ln f / 2 (Sec. 4.2).  Neither blocks. */
 rewl_status rewl_walk(rewl_handle* h);
 rewl_status rewl_flatness(rewl_handle* h);
+
+/* Conflict-table autotuner of the pipelined walker with the lattice in global memory (rewl_info
+ * .pipelined = 1, .lattice_in_shared = 0): times one walker launch of trial_moves (> 0) moves per
+ * walker for each table of 8192 down to 512 entries (at most one per site), keeps the fastest.
+ * A smaller table leaves more shared memory to L1 and fits more walkers per SM; sites sharing an
+ * entry cost extra exact corrections, never a different result.  The default is 1024 entries.
+ * Other handles have nothing to tune: their table stays and no move is made.  The timed moves are
+ * ordinary Wang-Landau moves: the walkers advance by them (walkers are initialised first if
+ * needed).  entries_out, ms_out (host, may be NULL) receive the chosen size and its trial time
+ * (0 when nothing was timed).  Blocks until the trials end. */
+rewl_status rewl_autotune(rewl_handle* h, int64_t trial_moves, int32_t* entries_out, double* ms_out);
 
 /* One replica-exchange round between adjacent windows (Sec. 4.3, Eq. 5): round t pairs windows
  * (k, k+1), k = t mod 2 (step 2), walker a with walker (a + floor(t/2)) mod m; a swap needs both

@@ -74,7 +74,7 @@ class Info(C.Structure):
                 ("e_min", C.c_double), ("e_max", C.c_double), ("bin_width", C.c_double),
                 ("initial_energy", C.c_double), ("exchange_index", C.c_int64), ("intervals_done", C.c_int64),
                 ("shared_bytes_per_walker", C.c_size_t), ("lattice_in_shared", C.c_int32),
-                ("pipelined", C.c_int32)]
+                ("pipelined", C.c_int32), ("conflict_entries", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -126,6 +126,7 @@ def load_library(path=LIB_PATH):
         "rewl_run_stage": ([_vp, C.POINTER(StageStats)], st),
         "rewl_exchange": ([_vp, C.POINTER(StageStats)], st),
         "rewl_walk": ([_vp], st),
+        "rewl_autotune": ([_vp, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double)], st),
         "rewl_flatness": ([_vp], st),
         "rewl_merge_lng": ([_vp, _vp, _vp], st),
         "rewl_merge_lng_device": ([_vp, _vp], st),
@@ -286,6 +287,13 @@ class REWL:
         s = StageStats()
         _check(self._lib.rewl_exchange(self._h, C.byref(s)), self._h)
         return s.as_dict()
+
+    def autotune(self, trial_moves=2000):
+        """Conflict-table size of a pipelined walker with the lattice in global memory, chosen by
+        timing; the trial moves are ordinary moves.  Returns {"conflict_entries", "trial_ms"}."""
+        e, ms = C.c_int32(), C.c_double()
+        _check(self._lib.rewl_autotune(self._h, int(trial_moves), C.byref(e), C.byref(ms)), self._h)
+        return {"conflict_entries": e.value, "trial_ms": ms.value}
 
     def walk(self):
         """Enqueue one interval of trial moves (walker kernel only); does not block."""

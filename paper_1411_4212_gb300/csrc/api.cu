@@ -16,6 +16,11 @@
 
 using namespace rewl;
 
+// Conflict-table entries of a pipelined walker whose lattice stays in global memory (rewl_autotune
+// may pick another size): bcc L = 32 with four shells ran fastest at 1024-2048 entries, at 4
+// walkers per SM, against 8192 entries at 2 per SM.
+constexpr int kGlobalLatticeOwnEntries = 1024;
+
 struct rewl_handle {
   int kind = 0, L = 0, N = 0, z = 0;
   int B = 0, h = 0, m = 0, W = 0, S = 0;
@@ -486,7 +491,9 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
       h->own_entries = e;
       h->pipe_smem_lattice = true;
     } else {
-      h->own_entries = own_full;
+      // lattice in global memory: a small table keeps the arena near 20 KB, so several walkers
+      // share an SM and most of its unified L1 stays free for the lattice gathers
+      h->own_entries = std::min(own_full, kGlobalLatticeOwnEntries);
       h->pipe_smem_lattice = false;
     }
     h->pipe_smem_bytes = walker_pipe_smem_bytes(h->traj, h->pipe_smem_lattice, h->N, h->W, h->own_entries);
@@ -494,15 +501,16 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   }
 
   const size_t S = h->S, W = h->W, N = h->N;
-  const size_t real = h->traj ? sizeof(double) : sizeof(float);
   rewl_status st = REWL_OK;
   auto A = [&](auto** p, size_t count) {
     if (st == REWL_OK) st = dev_alloc(h, p, count);
   };
+  // spins: FP64 planes [S][3][N] (trajectory) or FP32 quads (x, y, z, 0) [S][N] (production)
+  const size_t spin_bytes = h->traj ? S * 3 * N * sizeof(double) : S * N * sizeof(float4);
   void** spins_pp = &h->d_spins;
   {
     unsigned char* sp = nullptr;
-    A(&sp, S * 3 * N * real);
+    A(&sp, spin_bytes);
     *spins_pp = sp;
   }
   A(&h->d_perm, S);
@@ -554,16 +562,16 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
     if (ce == cudaSuccess) ce = cudaMemset(d, 0, bytes);
   };
   {
-    std::vector<unsigned char> sp(S * 3 * N * real, 0);
+    // every configuration starts aligned along z
+    std::vector<unsigned char> sp(spin_bytes, 0);
     for (size_t r = 0; r < S; ++r)
       for (size_t i = 0; i < N; ++i) {
-        const size_t idx = r * 3 * N + 2 * N + i;
         if (h->traj) {
           const double one = 1.0;
-          std::memcpy(sp.data() + idx * real, &one, real);
+          std::memcpy(sp.data() + (r * 3 * N + 2 * N + i) * sizeof(double), &one, sizeof one);
         } else {
           const float one = 1.0f;
-          std::memcpy(sp.data() + idx * real, &one, real);
+          std::memcpy(sp.data() + ((r * N + i) * 4 + 2) * sizeof(float), &one, sizeof one);
         }
       }
     up(h->d_spins, sp.data(), sp.size());
@@ -708,6 +716,54 @@ rewl_status rewl_walk(rewl_handle* h) {
   const WalkerArgs a = walker_args(h, false, recompute, h->exchange_interval);
   CUDA_TRY(h, launch_walk(h, a));
   h->intervals_done += 1;
+  return REWL_OK;
+}
+
+rewl_status rewl_autotune(rewl_handle* h, int64_t trial_moves, int32_t* entries_out, double* ms_out) {
+  rewl_status s = check_ready(h);
+  if (s != REWL_OK) return s;
+  if (trial_moves < 1) return fail(h, REWL_EINVAL, "trial_moves must be > 0");
+  if (entries_out) *entries_out = h->pipe ? h->own_entries : 0;
+  if (ms_out) *ms_out = 0.0;
+  if (!h->pipe || h->pipe_smem_lattice) return REWL_OK;
+  if (!h->initialized) {
+    s = rewl_init_walkers(h);
+    if (s != REWL_OK) return s;
+  }
+  int own_full = 256;
+  while (own_full < h->N && own_full < 8192) own_full *= 2;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(h, cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  const int e_prev = h->own_entries;
+  int best_e = e_prev;
+  double best = -1.0;
+  for (int cand = own_full; cand >= 512 && e == cudaSuccess; cand /= 2) {
+    h->own_entries = cand;
+    h->pipe_smem_bytes = walker_pipe_smem_bytes(h->traj, false, h->N, h->W, cand);
+    const WalkerArgs a = walker_args(h, false, false, trial_moves);
+    e = cudaEventRecord(e0, h->stream);
+    if (e == cudaSuccess) e = launch_walk(h, a);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && (best < 0 || ms < best)) {
+      best = ms;
+      best_e = cand;
+    }
+  }
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  h->own_entries = e == cudaSuccess ? best_e : e_prev;
+  h->pipe_smem_bytes = walker_pipe_smem_bytes(h->traj, false, h->N, h->W, h->own_entries);
+  if (e != cudaSuccess) return fail(h, REWL_ECUDA, std::string("autotune trial: ") + cudaGetErrorString(e));
+  int32_t err = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&err, h->d_ctrl, sizeof err, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (err != kErrNone) return fail(h, REWL_ESTATE, "walker kernel reported error " + std::to_string(err));
+  if (entries_out) *entries_out = h->own_entries;
+  if (ms_out) *ms_out = best;
   return REWL_OK;
 }
 
@@ -1048,6 +1104,7 @@ rewl_status rewl_get_info(const rewl_handle* hc, rewl_info* out) {
   out->shared_bytes_per_walker = h->pipe ? h->pipe_smem_bytes : h->smem_bytes;
   out->lattice_in_shared = (h->pipe ? h->pipe_smem_lattice : h->smem_lattice) ? 1 : 0;
   out->pipelined = h->pipe ? 1 : 0;
+  out->conflict_entries = h->pipe ? h->own_entries : 0;
   return REWL_OK;
 }
 
@@ -1106,10 +1163,14 @@ rewl_status rewl_get_spins(rewl_handle* h, double* spins) {
     CUDA_TRY(h, cudaMemcpyAsync(spins, h->d_spins, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   } else {
-    std::vector<float> t(n);
-    CUDA_TRY(h, cudaMemcpyAsync(t.data(), h->d_spins, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    // device quads (x, y, z, 0) per site -> host planes
+    const size_t N = h->N, R = h->S;
+    std::vector<float> t(R * N * 4);
+    CUDA_TRY(h, cudaMemcpyAsync(t.data(), h->d_spins, t.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    for (size_t i = 0; i < n; ++i) spins[i] = t[i];
+    for (size_t r = 0; r < R; ++r)
+      for (size_t c = 0; c < 3; ++c)
+        for (size_t i = 0; i < N; ++i) spins[(r * 3 + c) * N + i] = t[(r * N + i) * 4 + c];
   }
   return REWL_OK;
 }

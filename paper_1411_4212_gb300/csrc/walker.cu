@@ -25,11 +25,9 @@
 namespace rewl {
 
 // Warp 0: the walk.  All state below is warp-uniform unless named per-lane.
-template <bool kTraj>
+template <bool kTraj, class Lat>
 __device__ void walk(const WalkerArgs& a, int slot, int wlo, typename Mode<kTraj>::Lng* lng_s,
-                     uint32_t* H_s, const uint32_t* off_s, const typename Mode<kTraj>::Real* J_s,
-                     typename Mode<kTraj>::Real* sx, typename Mode<kTraj>::Real* sy,
-                     typename Mode<kTraj>::Real* sz) {
+                     uint32_t* H_s, const uint32_t* off_s, const typename Mode<kTraj>::Real* J_s, const Lat& lat) {
   using Real = typename Mode<kTraj>::Real;
   using Lng = typename Mode<kTraj>::Lng;
   const int lane = threadIdx.x & 31;
@@ -104,7 +102,7 @@ __device__ void walk(const WalkerArgs& a, int slot, int wlo, typename Mode<kTraj
       nz = (Real)fnz;
     }
     if (bcc) bcc_coords(site, a.geo.L, a.geo.divL, X, Y, Z);
-    const Real dE = delta_energy<kTraj>(a, off_s, J_s, sx, sy, sz, site, X, Y, Z, nx, ny, nz, sub, G, kFullMask);
+    const Real dE = delta_energy<kTraj>(a, off_s, J_s, lat, site, X, Y, Z, nx, ny, nz, sub, G, kFullMask);
     long long dq = 0;
     if (!kTraj) dq = __double2ll_rn((double)dE * a.win.dq_scale64);
 
@@ -157,7 +155,7 @@ __device__ void walk(const WalkerArgs& a, int slot, int wlo, typename Mode<kTraj
         const double u_k = __shfl_sync(kFullMask, u, src);
         if (cm & acc_mask) {
           double dn = 0.0;
-          if (g == k) dn = (double)delta_energy<kTraj>(a, off_s, J_s, sx, sy, sz, site, X, Y, Z, nx, ny, nz, sub, G, gmask);
+          if (g == k) dn = (double)delta_energy<kTraj>(a, off_s, J_s, lat, site, X, Y, Z, nx, ny, nz, sub, G, gmask);
           dE_k = __shfl_sync(kFullMask, dn, src);
           ++n_rec;
         }
@@ -195,7 +193,7 @@ __device__ void walk(const WalkerArgs& a, int slot, int wlo, typename Mode<kTraj
         if (cm & acc_mask) {
           long long dn = 0;
           if (g == k) {
-            const float dEn = (float)delta_energy<kTraj>(a, off_s, J_s, sx, sy, sz, site, X, Y, Z, nx, ny, nz, sub, G, gmask);
+            const float dEn = (float)delta_energy<kTraj>(a, off_s, J_s, lat, site, X, Y, Z, nx, ny, nz, sub, G, gmask);
             dn = __double2ll_rn((double)dEn * a.win.dq_scale64);
           }
           dq_k = shfl_ll(dn, src);
@@ -232,11 +230,7 @@ __device__ void walk(const WalkerArgs& a, int slot, int wlo, typename Mode<kTraj
       if (acc) {
         acc_mask |= 1u << k;
         ++n_acc;
-        if (lane == src) {
-          sx[site] = nx;
-          sy[site] = ny;
-          sz[site] = nz;
-        }
+        if (lane == src) lat.set(site, nx, ny, nz);
         __syncwarp();
       }
       if (!init && !frozen) {
@@ -293,10 +287,12 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_kernel(const WalkerArgs
   Real* J_s = reinterpret_cast<Real*>(off_s + kMaxSlotsPerSite);
   Real* spin_s = J_s + kMaxSlotsPerSite;
 
-  Real* gsp = reinterpret_cast<Real*>(a.st.spins) + (size_t)rep * 3 * N;
-  Real* sx = kSmem ? spin_s : gsp;
-  Real* sy = sx + N;
-  Real* sz = sx + 2 * (size_t)N;
+  const auto glat = GlobalLattice<kTraj>::of(a.st.spins, rep, N);
+  typename WalkLattice<kTraj, kSmem>::T lat;
+  if constexpr (kSmem)
+    lat = SpinPlanes<Real>(spin_s, N);
+  else
+    lat = glat;
 
   // stage tables and lattice
   const size_t lbase = (size_t)slot * W;
@@ -313,15 +309,13 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_kernel(const WalkerArgs
     off_s[j] = a.geo.off[j];
     J_s[j] = kTraj ? (Real)a.geo.Jd[j] : (Real)a.geo.Jf[j];
   }
-  if (kSmem)
-    for (size_t i = tid; i < 3 * (size_t)N; i += blockDim.x) spin_s[i] = gsp[i];
+  if constexpr (kSmem) copy_lattice(lat, glat, N, tid, blockDim.x);
   __syncthreads();
 
-  if (tid < 32) walk<kTraj>(a, slot, wlo, lng_s, H_s, off_s, J_s, sx, sy, sz);
+  if (tid < 32) walk<kTraj>(a, slot, wlo, lng_s, H_s, off_s, J_s, lat);
   __syncthreads();
 
-  if (kSmem)
-    for (size_t i = tid; i < 3 * (size_t)N; i += blockDim.x) gsp[i] = spin_s[i];
+  if constexpr (kSmem) copy_lattice(glat, lat, N, tid, blockDim.x);
   if (!a.init) {
     for (int w = tid; w < W; w += blockDim.x) {
       if (kTraj)
@@ -332,7 +326,7 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_kernel(const WalkerArgs
     }
   }
   if (a.recompute && !a.init) {
-    const double Ef = full_energy<kTraj>(a, off_s, sx, sy, sz, red, threadIdx.x, blockDim.x, 0);
+    const double Ef = full_energy<kTraj>(a, off_s, lat, red, threadIdx.x, blockDim.x, 0);
     if (tid == 0) {
       if (kTraj) {
         const double d = fabs(Ef - a.st.E[slot]);
@@ -355,14 +349,13 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_kernel(const WalkerArgs
 // FP64 energy of every configuration (one CTA each), spins read from global memory.
 template <bool kTraj>
 __global__ void __launch_bounds__(kWalkerThreads) energies_kernel(const WalkerArgs a, double* out) {
-  using Real = typename Mode<kTraj>::Real;
   __shared__ double red[kWalkerThreads / 32];
   __shared__ uint32_t off_s[kMaxSlotsPerSite];
   for (int j = threadIdx.x; j < kMaxSlotsPerSite; j += blockDim.x) off_s[j] = a.geo.off[j];
   __syncthreads();
   const int N = a.geo.N;
-  const Real* sp = reinterpret_cast<const Real*>(a.st.spins) + (size_t)blockIdx.x * 3 * N;
-  const double e = full_energy<kTraj>(a, off_s, sp, sp + N, sp + 2 * (size_t)N, red, threadIdx.x, blockDim.x, 0);
+  const auto lat = GlobalLattice<kTraj>::of(a.st.spins, blockIdx.x, N);
+  const double e = full_energy<kTraj>(a, off_s, lat, red, threadIdx.x, blockDim.x, 0);
   if (threadIdx.x == 0) out[blockIdx.x] = e;
 }
 

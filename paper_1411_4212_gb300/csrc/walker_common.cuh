@@ -20,17 +20,89 @@ struct Mode<false> {
   using Lng = long long;
 };
 
+// Spins of one configuration, in one of two layouts.
+// SpinPlanes: three arrays x[N], y[N], z[N] -- lattices in shared memory, and FP64 lattices in global
+//   memory ([R][3][N]).
+// SpinQuads: one (x, y, z, 0) float4 per site -- FP32 lattices in global memory ([R][N]): a
+//   neighbour's spin is one 16-byte load from one 32-byte sector instead of three loads from three.
+template <typename Real>
+struct SpinPlanes {
+  using Value = Real;
+  Real *x, *y, *z;
+  __device__ __forceinline__ SpinPlanes() : x(nullptr), y(nullptr), z(nullptr) {}
+  __device__ __forceinline__ SpinPlanes(Real* p, int N) : x(p), y(p + N), z(p + 2 * (size_t)N) {}
+  __device__ __forceinline__ void get(int i, Real& vx, Real& vy, Real& vz) const {
+    vx = x[i];
+    vy = y[i];
+    vz = z[i];
+  }
+  __device__ __forceinline__ void set(int i, Real vx, Real vy, Real vz) const {
+    x[i] = vx;
+    y[i] = vy;
+    z[i] = vz;
+  }
+};
+
+struct SpinQuads {
+  using Value = float;
+  float4* q;
+  __device__ __forceinline__ void get(int i, float& vx, float& vy, float& vz) const {
+    const float4 v = q[i];
+    vx = v.x;
+    vy = v.y;
+    vz = v.z;
+  }
+  __device__ __forceinline__ void set(int i, float vx, float vy, float vz) const {
+    q[i] = make_float4(vx, vy, vz, 0.0f);
+  }
+};
+
+// The global-memory lattice of configuration r: FP64 planes (trajectory) or FP32 quads (production).
+template <bool kTraj>
+struct GlobalLattice {
+  using T = SpinPlanes<double>;
+  static __device__ __forceinline__ T of(void* spins, int r, int N) {
+    return T(reinterpret_cast<double*>(spins) + (size_t)r * 3 * N, N);
+  }
+};
+template <>
+struct GlobalLattice<false> {
+  using T = SpinQuads;
+  static __device__ __forceinline__ T of(void* spins, int r, int N) {
+    return SpinQuads{reinterpret_cast<float4*>(spins) + (size_t)r * N};
+  }
+};
+
+// The lattice a walker reads: planes in shared memory, else the global layout of its mode.
+template <bool kTraj, bool kSmem>
+struct WalkLattice {
+  using T = SpinPlanes<typename Mode<kTraj>::Real>;
+};
+template <bool kTraj>
+struct WalkLattice<kTraj, false> {
+  using T = typename GlobalLattice<kTraj>::T;
+};
+
+// Copy N spins between layouts by the nt threads t of a group.
+template <class Dst, class Src>
+__device__ __forceinline__ void copy_lattice(const Dst& d, const Src& s, int N, int t, int nt) {
+  for (int i = t; i < N; i += nt) {
+    typename Src::Value vx, vy, vz;
+    s.get(i, vx, vy, vz);
+    d.set(i, vx, vy, vz);
+  }
+}
+
 __device__ __forceinline__ long long shfl_ll(long long v, int src) {
   return (long long)__shfl_sync(kFullMask, (unsigned long long)v, src);
 }
 
 // Energy change of moving spin `site` to (nx, ny, nz), evaluated by the G lanes of one group.
 // Summation order: lane `sub` sums slots sub, sub+G, ... in order; then xor butterfly G/2..1.
-template <bool kTraj>
+template <bool kTraj, class Lat>
 __device__ __forceinline__ typename Mode<kTraj>::Real delta_energy(
-    const WalkerArgs& a, const uint32_t* off_s, const typename Mode<kTraj>::Real* J_s,
-    const typename Mode<kTraj>::Real* sx, const typename Mode<kTraj>::Real* sy,
-    const typename Mode<kTraj>::Real* sz, int site, int X, int Y, int Z,
+    const WalkerArgs& a, const uint32_t* off_s, const typename Mode<kTraj>::Real* J_s, const Lat& lat,
+    int site, int X, int Y, int Z,
     typename Mode<kTraj>::Real nx, typename Mode<kTraj>::Real ny, typename Mode<kTraj>::Real nz,
     int sub, int G, unsigned mask) {
   using Real = typename Mode<kTraj>::Real;
@@ -47,10 +119,12 @@ __device__ __forceinline__ typename Mode<kTraj>::Real delta_energy(
       unpack_offset(o, dx, dy, dz);
       const int n = bcc_offset_site(X, Y, Z, dx, dy, dz, L);
       const Real J = J_s[j];
+      Real vx, vy, vz;
+      lat.get(n, vx, vy, vz);
       if (kTraj) {
-        hx = __dadd_rn(hx, __dmul_rn(J, sx[n]));
-        hy = __dadd_rn(hy, __dmul_rn(J, sy[n]));
-        hz = __dadd_rn(hz, __dmul_rn(J, sz[n]));
+        hx = __dadd_rn(hx, __dmul_rn(J, vx));
+        hy = __dadd_rn(hy, __dmul_rn(J, vy));
+        hz = __dadd_rn(hz, __dmul_rn(J, vz));
       } else {
         const uint32_t sh = o >> 24;
         if (sh != shc) {
@@ -61,9 +135,9 @@ __device__ __forceinline__ typename Mode<kTraj>::Real delta_energy(
           shc = sh;
           Jcur = J;
         }
-        tx += sx[n];
-        ty += sy[n];
-        tz += sz[n];
+        tx += vx;
+        ty += vy;
+        tz += vz;
       }
     }
     if (!kTraj) {
@@ -74,16 +148,18 @@ __device__ __forceinline__ typename Mode<kTraj>::Real delta_energy(
   } else {
     for (int j = sub; j < z; j += G) {
       const int n = __ldg(a.geo.tab_nbr + (size_t)j * N + site);
+      Real vx, vy, vz;
+      lat.get(n, vx, vy, vz);
       if (kTraj) {
         const double J = __ldg(a.geo.tab_Jd + (size_t)j * N + site);
-        hx = __dadd_rn(hx, __dmul_rn(J, sx[n]));
-        hy = __dadd_rn(hy, __dmul_rn(J, sy[n]));
-        hz = __dadd_rn(hz, __dmul_rn(J, sz[n]));
+        hx = __dadd_rn(hx, __dmul_rn(J, vx));
+        hy = __dadd_rn(hy, __dmul_rn(J, vy));
+        hz = __dadd_rn(hz, __dmul_rn(J, vz));
       } else {
         const float J = __ldg(a.geo.tab_Jf + (size_t)j * N + site);
-        hx = fmaf(J, sx[n], hx);
-        hy = fmaf(J, sy[n], hy);
-        hz = fmaf(J, sz[n], hz);
+        hx = fmaf(J, vx, hx);
+        hy = fmaf(J, vy, hy);
+        hz = fmaf(J, vz, hz);
       }
     }
   }
@@ -101,7 +177,8 @@ __device__ __forceinline__ typename Mode<kTraj>::Real delta_energy(
       hz += pz;
     }
   }
-  const Real ox = sx[site], oy = sy[site], oz = sz[site];
+  Real ox, oy, oz;
+  lat.get(site, ox, oy, oz);
   if (kTraj) {
     const double dx = __dsub_rn(nx, ox), dy = __dsub_rn(ny, oy), dz = __dsub_rn(nz, oz);
     return -__dadd_rn(__dadd_rn(__dmul_rn(dx, hx), __dmul_rn(dy, hy)), __dmul_rn(dz, hz));
@@ -224,10 +301,10 @@ __device__ __forceinline__ double block_sum_double(double v, double* red, int t,
 
 // Full energy of a configuration, E = -w sum_i sum_{energy slots} J S_i.S_n, by the nt threads
 // t = 0..nt-1 of a group that synchronises on barrier bar; valid in thread t = 0.
-template <bool kTraj>
-__device__ double full_energy(const WalkerArgs& a, const uint32_t* off_s,
-                              const typename Mode<kTraj>::Real* sx, const typename Mode<kTraj>::Real* sy,
-                              const typename Mode<kTraj>::Real* sz, double* red, int t, int nt, int bar) {
+template <bool kTraj, class Lat>
+__device__ double full_energy(const WalkerArgs& a, const uint32_t* off_s, const Lat& lat, double* red, int t,
+                              int nt, int bar) {
+  using Real = typename Mode<kTraj>::Real;
   const int N = a.geo.N;
   const bool bcc = a.geo.kind == 0;
   double part = 0.0;
@@ -250,11 +327,15 @@ __device__ double full_energy(const WalkerArgs& a, const uint32_t* off_s,
           n = a.geo.tab_nbr[(size_t)j * N + i];
           J = a.geo.tab_Jd[(size_t)j * N + i];
         }
-        hx += J * sx[n];
-        hy += J * sy[n];
-        hz += J * sz[n];
+        Real vx, vy, vz;
+        lat.get(n, vx, vy, vz);
+        hx += J * vx;
+        hy += J * vy;
+        hz += J * vz;
       }
-      part += sx[i] * hx + sy[i] * hy + sz[i] * hz;
+      Real six, siy, siz;
+      lat.get(i, six, siy, siz);
+      part += six * hx + siy * hy + siz * hz;
     } else {
       // float-float throughout: with nearly parallel spins every site has nearly the same field,
       // so plain FP32 rounding errors would add up coherently over N sites
@@ -272,16 +353,20 @@ __device__ double full_energy(const WalkerArgs& a, const uint32_t* off_s,
           n = a.geo.tab_nbr[(size_t)j * N + i];
           J = a.geo.tab_Jf[(size_t)j * N + i];
         }
+        Real vx, vy, vz;
+        lat.get(n, vx, vy, vz);
         float p, pe;
-        two_prod(J, (float)sx[n], p, pe);
+        two_prod(J, (float)vx, p, pe);
         ff_add(hxh, hxl, p, pe);
-        two_prod(J, (float)sy[n], p, pe);
+        two_prod(J, (float)vy, p, pe);
         ff_add(hyh, hyl, p, pe);
-        two_prod(J, (float)sz[n], p, pe);
+        two_prod(J, (float)vz, p, pe);
         ff_add(hzh, hzl, p, pe);
       }
       float p, pe;
-      const float six = (float)sx[i], siy = (float)sy[i], siz = (float)sz[i];
+      Real rx, ry, rz;
+      lat.get(i, rx, ry, rz);
+      const float six = (float)rx, siy = (float)ry, siz = (float)rz;
       two_prod(six, hxh, p, pe);
       ff_add(hi, lo, p, fmaf(six, hxl, pe));
       two_prod(siy, hyh, p, pe);

@@ -85,11 +85,8 @@ struct alignas(16) Rec<true> {
 
 // Local field of (X, Y, Z) by one lane over all slots in canonical order, with the owner-table
 // words of the site's neighbours OR-ed into own0 / own1 (kOwn).
-template <bool kTraj, int NSH, bool kOwn = true>
-__device__ __forceinline__ void field_one_lane(const typename Mode<kTraj>::Real* __restrict__ sx,
-                                               const typename Mode<kTraj>::Real* __restrict__ sy,
-                                               const typename Mode<kTraj>::Real* __restrict__ sz, int X, int Y, int Z,
-                                               int L, const typename Mode<kTraj>::Real (&Jsh)[4],
+template <bool kTraj, int NSH, bool kOwn = true, class Lat>
+__device__ __forceinline__ void field_one_lane(const Lat& lat, int X, int Y, int Z, int L, const typename Mode<kTraj>::Real (&Jsh)[4],
                                                typename Mode<kTraj>::Real& hx, typename Mode<kTraj>::Real& hy,
                                                typename Mode<kTraj>::Real& hz, const uint2* own, uint32_t omask,
                                                uint32_t& own0, uint32_t& own1) {
@@ -123,15 +120,17 @@ __device__ __forceinline__ void field_one_lane(const typename Mode<kTraj>::Real*
 #pragma unroll
   for (int j = 0; j < T.z; ++j) {
     const int n = xw[T.dx[j] + 3] + yw[T.dy[j] + 3] + zw[T.dz[j] + 3] - ((T.dx[j] & 1) ? par_flip : par_same);
+    Real vx, vy, vz;
+    lat.get(n, vx, vy, vz);
     if constexpr (kTraj) {
       const Real J = Jsh[T.sh[j]];
-      hx = __dadd_rn(hx, __dmul_rn(J, sx[n]));
-      hy = __dadd_rn(hy, __dmul_rn(J, sy[n]));
-      hz = __dadd_rn(hz, __dmul_rn(J, sz[n]));
+      hx = __dadd_rn(hx, __dmul_rn(J, vx));
+      hy = __dadd_rn(hy, __dmul_rn(J, vy));
+      hz = __dadd_rn(hz, __dmul_rn(J, vz));
     } else {
-      tx[T.sh[j]] += sx[n];
-      ty[T.sh[j]] += sy[n];
-      tz[T.sh[j]] += sz[n];
+      tx[T.sh[j]] += vx;
+      ty[T.sh[j]] += vy;
+      tz[T.sh[j]] += vz;
     }
     if constexpr (kOwn) {
       const uint2 o = own[n & omask];
@@ -199,10 +198,12 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
   p += sizeof(uint2) * ((size_t)omask + 1);
   Real* spin_s = reinterpret_cast<Real*>(p);
 
-  Real* gsp = reinterpret_cast<Real*>(a.st.spins) + (size_t)rep * 3 * N;
-  Real* sx = kSmem ? spin_s : gsp;
-  Real* sy = sx + N;
-  Real* sz = sx + 2 * (size_t)N;
+  const auto glat = GlobalLattice<kTraj>::of(a.st.spins, rep, N);
+  typename WalkLattice<kTraj, kSmem>::T lat;
+  if constexpr (kSmem)
+    lat = SpinPlanes<Real>(spin_s, N);
+  else
+    lat = glat;
 
   const size_t lbase = (size_t)slot * W;
   for (int w = tid; w < W; w += nt) {
@@ -217,8 +218,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
     J_s[j] = kTraj ? (Real)a.geo.Jd[j] : (Real)a.geo.Jf[j];
   }
   for (uint32_t i = tid; i <= omask; i += nt) own[i] = make_uint2(0u, 0u);
-  if (kSmem)
-    for (size_t i = tid; i < 3 * (size_t)N; i += nt) spin_s[i] = gsp[i];
+  if constexpr (kSmem) copy_lattice(lat, glat, N, tid, nt);
   group_sync(bar_sync, nt);
 
   const int nb = (int)((moves + 31) / 32);
@@ -268,12 +268,13 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       __syncwarp();
       uint32_t o0 = 0, o1 = 0;
       Real hx, hy, hz;
-      field_one_lane<kTraj, NSH>(sx, sy, sz, X, Y, Z, L, Jsh, hx, hy, hz, own, omask, o0, o1);
+      field_one_lane<kTraj, NSH>(lat, X, Y, Z, L, Jsh, hx, hy, hz, own, omask, o0, o1);
       const uint2 oself = own[site & omask];
       o0 |= oself.x;
       o1 |= oself.y;
       const uint32_t ocur = cur ? o1 : o0, oprev = cur ? o0 : o1;
-      const Real ox = sx[site], oy = sy[site], oz = sz[site];
+      Real ox, oy, oz;
+      lat.get(site, ox, oy, oz);
       Rec<kTraj>& r = rec[cur * 32 + lane];
       if constexpr (kTraj) {
         const double dx = __dsub_rn(nx, ox), dy = __dsub_rn(ny, oy), dz = __dsub_rn(nz, oz);
@@ -381,7 +382,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
             bcc_coords(site, L, a.geo.divL, X, Y, Z);
             double dn = 0.0;
             if (lane == 0)
-              dn = (double)delta_energy<true>(a, off_s, J_s, sx, sy, sz, site, X, Y, Z, r.nx, r.ny, r.nz, 0, 1, 1u);
+              dn = (double)delta_energy<true>(a, off_s, J_s, lat, site, X, Y, Z, r.nx, r.ny, r.nz, 0, 1, 1u);
             dE = __shfl_sync(kFullMask, dn, 0);
             ++n_rec;
           }
@@ -410,7 +411,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
             __syncwarp();
             int X, Y, Z;
             bcc_coords(site, L, a.geo.divL, X, Y, Z);
-            const float dEn = (float)delta_energy<false>(a, off_s, J_s, sx, sy, sz, site, X, Y, Z, r.nx, r.ny, r.nz,
+            const float dEn = (float)delta_energy<false>(a, off_s, J_s, lat, site, X, Y, Z, r.nx, r.ny, r.nz,
                                                          lane, 32, kFullMask);
             dq = dq24_of(dEn, a.win);
             ++n_rec;
@@ -449,11 +450,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         if (acc) {
           acc_cur |= 1u << k;
           ++n_acc;
-          if (lane == 0) {
-            sx[site] = r.nx;
-            sy[site] = r.ny;
-            sz[site] = r.nz;
-          }
+          if (lane == 0) lat.set(site, r.nx, r.ny, r.nz);
         }
         if (!frozen) {
           if constexpr (kTraj)
@@ -554,9 +551,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
     auto publish = [&](const Rec<false>* R, uint32_t acc) {
       if ((acc >> lane) & 1u) {
         const Rec<false>& rp = R[lane];
-        sx[rp.site] = rp.nx;
-        sy[rp.site] = rp.ny;
-        sz[rp.site] = rp.nz;
+        lat.set(rp.site, rp.nx, rp.ny, rp.nz);
       }
       __syncwarp();
     };
@@ -857,8 +852,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
   }
   group_sync(bar_sync, nt);
 
-  if (kSmem)
-    for (size_t i = tid; i < 3 * (size_t)N; i += nt) gsp[i] = spin_s[i];
+  if constexpr (kSmem) copy_lattice(glat, lat, N, tid, nt);
   for (int w = tid; w < W; w += nt) {
     if constexpr (kTraj)
       a.st.lng[lbase + w] = (double)lng_s[w];
@@ -867,7 +861,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
     a.st.H[lbase + w] = H_s[w];
   }
   if (recompute) {
-    const double Ef = full_energy<kTraj>(a, off_s, sx, sy, sz, red, tid, nt, bar_sync);
+    const double Ef = full_energy<kTraj>(a, off_s, lat, red, tid, nt, bar_sync);
     if (tid == 0) {
       if constexpr (kTraj) {
         const double d = fabs(Ef - a.st.E[slot]);

@@ -76,5 +76,6 @@ def test_batch_entry_points_reject_invalid_arguments():
     assert lib.rewl_batch_get_info(None, None) == rw.EINVAL
     assert lib.rewl_batch_run_intervals(None, 1) == rw.EINVAL
     assert lib.rewl_batch_autotune(None, 10, None, None) == rw.EINVAL
+    assert lib.rewl_autotune(None, 10, None, None) == rw.EINVAL
     assert lib.rewl_batch_run_to_convergence(None, 1, 1, None) == rw.EINVAL
     lib.rewl_batch_destroy(None)

@@ -109,6 +109,37 @@ def test_global_memory_lattice_path():
     gpu.close()
 
 
+def test_global_memory_lattice_autotune_moves_are_ordinary_moves():
+    """The conflict-table autotuner times five walker launches (8192 .. 512 entries, aliasing up to 32
+    sites per entry): each is ordinary moves, so the oracle walking the same count agrees bit for bit,
+    and so do the intervals after it on the chosen table."""
+    gpu, orc = make_pair(group_size=1, L=20, J=(1.0, 0.5), n_bins=400, n_windows=3, walkers_per_window=1,
+                         overlap=0.75, flatness=0.8, lnf_final=1e-8, seed=3, exchange_interval=1500)
+    assert gpu.info()["conflict_entries"] == 1024
+    gpu.init_walkers()
+    orc.init_walkers()
+    t = gpu.autotune(trial_moves=300)
+    assert t["conflict_entries"] in (512, 1024, 2048, 4096, 8192) and t["trial_ms"] > 0
+    assert gpu.info()["conflict_entries"] == t["conflict_entries"]
+    orc.run_moves_only(5 * 300)
+    assert_same_state(gpu, orc)
+    gpu.run_intervals(2)
+    orc.run_intervals(2)
+    assert_same_state(gpu, orc)
+    gpu.close()
+
+
+def test_autotune_leaves_shared_lattice_walkers_alone():
+    gpu, _ = make_pair(group_size=1, exchange_interval=1000, **CFG1)
+    gpu.init_walkers()
+    steps = gpu.walkers()["steps"].copy()
+    entries = gpu.info()["conflict_entries"]
+    t = gpu.autotune(trial_moves=300)
+    assert t == {"conflict_entries": entries, "trial_ms": 0.0}
+    assert np.array_equal(gpu.walkers()["steps"], steps)
+    gpu.close()
+
+
 def test_frozen_walkers_and_set_initial_lng():
     """Warm start: set ln g and ln f below ln f_final for every walker (frozen), walk, compare."""
     gpu, orc = make_pair(group_size=8, exchange_interval=1000, **CFG1)
