@@ -532,8 +532,13 @@ def main():
     walker_share = sum(walk_ms) / sum(step_ms)
     pipelined = bool(sim.info()["pipelined"])
     in_smem = "true" if sim.info()["lattice_in_shared"] else "false"
-    kernel = (f"walker_pipe_kernel<false,{in_smem},{len(workload['J'])}>" if pipelined
-              else f"walker_kernel<false,{in_smem}>")
+    nsh = len(workload["J"])
+    if not pipelined:
+        kernel = f"walker_kernel<false,{in_smem}>"
+    elif in_smem == "true":
+        kernel = f"walker_pipe_kernel<false,{nsh}>"
+    else:
+        kernel = f"walker_pipe_global_kernel<false,{nsh}>"
     traffic = profiled_traffic(kernel, S * workload["exchange_interval"])
 
     # end to end through the public API with host buffers: ln g in (warm start), merged ln g out

@@ -181,9 +181,10 @@ rewl_status rewl_flatness(rewl_handle* h);
 
 /* Conflict-table autotuner of the pipelined walker with the lattice in global memory (rewl_info
  * .pipelined = 1, .lattice_in_shared = 0): times one walker launch of trial_moves (> 0) moves per
- * walker for each table of 8192 down to 512 entries (at most one per site), keeps the fastest.
+ * walker for each table of 8192 down to 512 entries (at most one per site), twice (the second round
+ * in reverse order), and keeps the table with the fastest trial.
  * A smaller table leaves more shared memory to L1 and fits more walkers per SM; sites sharing an
- * entry cost extra exact corrections, never a different result.  The default is 1024 entries.
+ * entry cost extra exact corrections, never a different result.  The default is 2048 entries.
  * Other handles have nothing to tune: their table stays and no move is made.  The timed moves are
  * ordinary Wang-Landau moves: the walkers advance by them (walkers are initialised first if
  * needed).  entries_out, ms_out (host, may be NULL) receive the chosen size and its trial time
@@ -334,7 +335,8 @@ rewl_status rewl_batch_set_tuning(rewl_batch* b, const rewl_batch_tuning* t);
 
 /* Autotuner: time one walker launch of trial_moves moves per walker (> 0) for every candidate
  * (workers_per_block 1..3 x every lattice-size threshold of the batch's jobs x conflict tables of
- * 8192 down to 512 entries), keep the fastest.
+ * 8192 down to 512 entries), twice (the second round in reverse order); keep the candidate with the
+ * fastest trial.
  * The timed moves are ordinary Wang-Landau moves of the jobs: the walkers advance by them.
  * chosen (host, may be NULL) receives the tuning; ms_out (host, may be NULL) its trial time. */
 rewl_status rewl_batch_autotune(rewl_batch* b, int64_t trial_moves, rewl_batch_tuning* chosen, double* ms_out);

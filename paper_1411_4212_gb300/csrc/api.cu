@@ -17,9 +17,10 @@
 using namespace rewl;
 
 // Conflict-table entries of a pipelined walker whose lattice stays in global memory (rewl_autotune
-// may pick another size): bcc L = 32 with four shells ran fastest at 1024-2048 entries, at 4
-// walkers per SM, against 8192 entries at 2 per SM.
-constexpr int kGlobalLatticeOwnEntries = 1024;
+// may pick another size): bcc L = 32 with four shells ran fastest at 2048 entries.  Larger tables
+// take shared memory from L1 and fit fewer walkers per SM; smaller ones make sites share entries
+// often enough that the extra corrections cost more.
+constexpr int kGlobalLatticeOwnEntries = 2048;
 
 struct rewl_handle {
   int kind = 0, L = 0, N = 0, z = 0;
@@ -65,6 +66,9 @@ struct rewl_handle {
   long long* d_init_moves = nullptr;
   double* d_drift = nullptr;
   int32_t* d_ctrl = nullptr;
+  WalkerArgs* d_wargs = nullptr;   // pipelined walker over a global-memory lattice: its arguments
+  WalkerArgs wargs_host{};         // what d_wargs holds (moves and recompute zeroed)
+  bool wargs_valid = false;
   long long* d_ex_index = nullptr;
   int32_t* d_rt_last = nullptr;
   long long* d_rt_count = nullptr;
@@ -231,12 +235,29 @@ WalkerArgs walker_args(rewl_handle* h, bool init, bool recompute, long long move
   a.recompute = recompute ? 1 : 0;
   a.lnf_final = h->lnf_final;
   a.own_mask = h->own_entries > 0 ? h->own_entries - 1 : 0;
+  a.smem_lattice = (h->pipe ? h->pipe_smem_lattice : h->smem_lattice) ? 1 : 0;
   return a;
 }
 
 // The Wang-Landau moves of one exchange interval (the initial drive always uses the batch walker).
 cudaError_t launch_walk(rewl_handle* h, const WalkerArgs& a) {
-  if (h->pipe) return launch_walkers_pipe(a, h->S, h->traj, h->pipe_smem_lattice, h->pipe_smem_bytes, h->stream);
+  if (h->pipe && h->pipe_smem_lattice)
+    return launch_walkers_pipe(a, nullptr, h->S, h->traj, h->pipe_smem_bytes, h->stream);
+  if (h->pipe) {
+    // the global-memory walker reads its arguments from d_wargs: upload them when they change
+    // (the pageable source is staged before the call returns, so wargs_host may change again)
+    WalkerArgs s = a;
+    s.moves = 0;
+    s.recompute = 0;
+    if (!h->wargs_valid || std::memcmp(&s, &h->wargs_host, sizeof s) != 0) {
+      h->wargs_host = s;
+      const cudaError_t e =
+          cudaMemcpyAsync(h->d_wargs, &h->wargs_host, sizeof(WalkerArgs), cudaMemcpyHostToDevice, h->stream);
+      if (e != cudaSuccess) return e;
+      h->wargs_valid = true;
+    }
+    return launch_walkers_pipe(a, h->d_wargs, h->S, h->traj, h->pipe_smem_bytes, h->stream);
+  }
   return launch_walkers(a, h->S, h->traj, h->smem_lattice, h->smem_bytes, h->stream);
 }
 
@@ -532,6 +553,7 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   A(&h->d_init_moves, S);
   A(&h->d_drift, S);
   A(&h->d_ctrl, 4);
+  A(&h->d_wargs, 1);
   A(&h->d_ex_index, 1);
   A(&h->d_rt_last, S);
   A(&h->d_rt_count, S);
@@ -736,23 +758,32 @@ rewl_status rewl_autotune(rewl_handle* h, int64_t trial_moves, int32_t* entries_
   CUDA_TRY(h, cudaEventCreate(&e0));
   cudaError_t e = cudaEventCreate(&e1);
   const int e_prev = h->own_entries;
-  int best_e = e_prev;
-  double best = -1.0;
-  for (int cand = own_full; cand >= 512 && e == cudaSuccess; cand /= 2) {
-    h->own_entries = cand;
-    h->pipe_smem_bytes = walker_pipe_smem_bytes(h->traj, false, h->N, h->W, cand);
-    const WalkerArgs a = walker_args(h, false, false, trial_moves);
-    e = cudaEventRecord(e0, h->stream);
-    if (e == cudaSuccess) e = launch_walk(h, a);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e == cudaSuccess && (best < 0 || ms < best)) {
-      best = ms;
-      best_e = cand;
+  // two rounds, the second in reverse order; each candidate keeps its faster trial
+  std::vector<int> cands;
+  for (int c = own_full; c >= 512; c /= 2) cands.push_back(c);
+  std::vector<double> t_min(cands.size(), -1.0);
+  for (int round = 0; round < 2 && e == cudaSuccess; ++round) {
+    for (size_t k = 0; k < cands.size() && e == cudaSuccess; ++k) {
+      const size_t c = round == 0 ? k : cands.size() - 1 - k;
+      h->own_entries = cands[c];
+      h->pipe_smem_bytes = walker_pipe_smem_bytes(h->traj, false, h->N, h->W, cands[c]);
+      const WalkerArgs a = walker_args(h, false, false, trial_moves);
+      e = cudaEventRecord(e0, h->stream);
+      if (e == cudaSuccess) e = launch_walk(h, a);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && (t_min[c] < 0 || ms < t_min[c])) t_min[c] = ms;
     }
   }
+  int best_e = e_prev;
+  double best = -1.0;
+  for (size_t c = 0; c < cands.size(); ++c)
+    if (t_min[c] >= 0 && (best < 0 || t_min[c] < best)) {
+      best = t_min[c];
+      best_e = cands[c];
+    }
   cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   h->own_entries = e == cudaSuccess ? best_e : e_prev;

@@ -394,18 +394,26 @@ extern "C" rewl_status rewl_batch_autotune(rewl_batch* b, int64_t trial_moves, r
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BCUDA(b, cudaEventCreate(&e0));
   BCUDA(b, cudaEventCreate(&e1));
-  double best = -1.0;
-  int best_w = b->workers, best_n = b->smem_max_n, best_c = b->own_cap;
+  // candidates that fit; a smaller cap is a new candidate only if it shrinks some job's table
+  struct Cand {
+    int w, thr, cap;
+    double ms;
+  };
+  std::vector<Cand> cands;
   for (int own_cap : {8192, 4096, 2048, 1024, 512})
-  for (int w = 1; w <= kBatchMaxWorkers; ++w) {
-    for (int thr : thresholds) {
-      if (apply_tuning(b, w, thr, own_cap) != REWL_OK) continue;   // does not fit: not a candidate
-      if (own_cap < 8192) {   // a smaller cap is a new candidate only if it shrinks some job's table
-        bool shrinks = false;
+    for (int w = 1; w <= kBatchMaxWorkers; ++w)
+      for (int thr : thresholds) {
+        if (apply_tuning(b, w, thr, own_cap) != REWL_OK) continue;
+        bool shrinks = own_cap == 8192;
         for (int j : b->active_ids)
           shrinks = shrinks || (!b->wargs[j].smem_lattice && b->view[j].N > own_cap);
-        if (!shrinks) continue;
+        if (shrinks) cands.push_back({w, thr, own_cap, -1.0});
       }
+  // two rounds, the second in reverse order; each candidate keeps its faster trial
+  for (int round = 0; round < 2; ++round) {
+    for (size_t k = 0; k < cands.size(); ++k) {
+      Cand& c = cands[round == 0 ? k : cands.size() - 1 - k];
+      if (apply_tuning(b, c.w, c.thr, c.cap) != REWL_OK) continue;
       cudaError_t e = cudaEventRecord(e0, b->stream);
       if (e == cudaSuccess) e = launch_walkers_batch(walker_launch(b, trial_moves, 0), b->stream);
       if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
@@ -417,14 +425,18 @@ extern "C" rewl_status rewl_batch_autotune(rewl_batch* b, int64_t trial_moves, r
         cudaEventDestroy(e1);
         return bfail(b, REWL_ECUDA, std::string("autotune trial: ") + cudaGetErrorString(e));
       }
-      if (best < 0 || ms < best) {
-        best = ms;
-        best_w = w;
-        best_n = thr;
-        best_c = own_cap;
-      }
+      if (c.ms < 0 || ms < c.ms) c.ms = ms;
     }
   }
+  double best = -1.0;
+  int best_w = b->workers, best_n = b->smem_max_n, best_c = b->own_cap;
+  for (const Cand& c : cands)
+    if (c.ms >= 0 && (best < 0 || c.ms < best)) {
+      best = c.ms;
+      best_w = c.w;
+      best_n = c.thr;
+      best_c = c.cap;
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   s = apply_tuning(b, best_w, best_n, best_c);

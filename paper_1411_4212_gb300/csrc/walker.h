@@ -15,7 +15,10 @@ cudaError_t launch_walkers(const WalkerArgs& a, int n_slots, bool traj, bool sme
 
 // Warp-specialised walker (bcc lattices, one lane per trial move, Wang-Landau moves only).
 size_t walker_pipe_smem_bytes(bool traj, bool smem_lattice, int N, int W, int own_entries);
-cudaError_t launch_walkers_pipe(const WalkerArgs& a, int n_slots, bool traj, bool smem_lattice, size_t smem,
+// a.smem_lattice selects the form: 1 = lattice in shared memory, arguments passed by value (d_args
+// NULL); 0 = lattice in global memory, the kernel reads d_args, a device copy of a (a.moves and
+// a.recompute are passed by value and may differ from the copy).
+cudaError_t launch_walkers_pipe(const WalkerArgs& a, const WalkerArgs* d_args, int n_slots, bool traj, size_t smem,
                                 cudaStream_t stream);
 
 // Batched pipelined walker: one persistent launch over (job, slot) items of many jobs with the same

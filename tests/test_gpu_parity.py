@@ -110,18 +110,18 @@ def test_global_memory_lattice_path():
 
 
 def test_global_memory_lattice_autotune_moves_are_ordinary_moves():
-    """The conflict-table autotuner times five walker launches (8192 .. 512 entries, aliasing up to 32
+    """The conflict-table autotuner times ten walker launches (8192 .. 512 entries, twice; up to 32
     sites per entry): each is ordinary moves, so the oracle walking the same count agrees bit for bit,
     and so do the intervals after it on the chosen table."""
     gpu, orc = make_pair(group_size=1, L=20, J=(1.0, 0.5), n_bins=400, n_windows=3, walkers_per_window=1,
                          overlap=0.75, flatness=0.8, lnf_final=1e-8, seed=3, exchange_interval=1500)
-    assert gpu.info()["conflict_entries"] == 1024
+    assert gpu.info()["conflict_entries"] == 2048
     gpu.init_walkers()
     orc.init_walkers()
     t = gpu.autotune(trial_moves=300)
     assert t["conflict_entries"] in (512, 1024, 2048, 4096, 8192) and t["trial_ms"] > 0
     assert gpu.info()["conflict_entries"] == t["conflict_entries"]
-    orc.run_moves_only(5 * 300)
+    orc.run_moves_only(10 * 300)
     assert_same_state(gpu, orc)
     gpu.run_intervals(2)
     orc.run_intervals(2)
