@@ -262,10 +262,10 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
-# DRAM traffic of the walker kernel, taken from the committed ncu summary of the same kernel.  The
-# summary records a hash of the kernel's sources; once they change the figure no longer applies and
-# the traffic is reported as null.
-PROFILE = os.path.join(ROOT, "profiles", "walker_pipe_cfg2.md")
+# DRAM traffic of the walker kernel, taken from the committed ncu summary of the same kernel (the
+# summary under profiles/ whose `kernel` field names it).  The summary records a hash of the
+# kernel's sources; once they change the figure no longer applies and the traffic is reported as null.
+PROFILES = os.path.join(ROOT, "profiles")
 KERNEL_SOURCES = ["walker_pipe.cu", "walker_common.cuh", "device_common.cuh", "rewl_types.h"]
 
 
@@ -278,21 +278,42 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def profiled_traffic(kernel, moves_per_launch):
-    """dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled from the profiled launch."""
-    if not os.path.exists(PROFILE):
-        return None
+def profile_fields(path):
     fields = {}
-    for line in open(PROFILE):
+    for line in open(path):
         if line.startswith("- ") and ": " in line:
             k, v = line[2:].split(": ", 1)
             fields[k.strip()] = v.strip().strip("`")
-    try:
-        if fields["kernel"] != kernel or fields["source_sha256"] != kernel_source_hash():
-            return None
-        return float(fields["dram_bytes_per_launch"]) * moves_per_launch / float(fields["moves_per_launch"])
-    except (KeyError, ValueError):
+    return fields
+
+
+def profiled_traffic(kernel, moves_per_launch):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled from the profiled launch."""
+    if not os.path.isdir(PROFILES):
         return None
+    for name in sorted(os.listdir(PROFILES)):
+        if not name.endswith(".md"):
+            continue
+        fields = profile_fields(os.path.join(PROFILES, name))
+        if fields.get("kernel") != kernel:
+            continue
+        try:
+            if fields["source_sha256"] != kernel_source_hash():
+                return None
+            return float(fields["dram_bytes_per_launch"]) * moves_per_launch / float(fields["moves_per_launch"])
+        except (KeyError, ValueError):
+            return None
+    return None
+
+
+def hbm_peak():
+    """Measured HBM copy bandwidth of this machine's GPUs (bytes/s) and where it comes from."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]) * 1e9, "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
+    except (OSError, KeyError, ValueError):
+        return 6.8e12, "fallback 6.8 TB/s (no measured peak file)"
 
 
 def run_batch64(args):
@@ -523,15 +544,25 @@ def main():
     acc_rate = (c1["accepts"] - c0["accepts"]) / max(1, c1["moves"] - c0["moves"])
     rec_rate = (c1["recomputes"] - c0["recomputes"]) / max(1, c1["moves"] - c0["moves"])
 
-    # roofline of the walker kernel against the shared-memory bandwidth of this GPU
+    # roofline of the walker kernel: lattices in shared memory against the shared-memory bandwidth
+    # of this GPU (neighbour spins, ln g and H, records); lattices in global memory against HBM
+    # (the lattice bytes alone: FP32 components of the z neighbours and the old spin, the accepted
+    # new spin written back)
     z = sim.z
-    bytes_per_move = 12 * z + 12 + 2 * 8 + 8 + 4 + 12 * acc_rate
     walk_avg_ms = statistics.mean(walk_ms)
-    achieved = bytes_per_move * S * workload["exchange_interval"] / (walk_avg_ms * 1e-3)
-    smem_peak, _ = rw.measure_smem_bandwidth(stream)
     walker_share = sum(walk_ms) / sum(step_ms)
     pipelined = bool(sim.info()["pipelined"])
     in_smem = "true" if sim.info()["lattice_in_shared"] else "false"
+    if in_smem == "true":
+        bound = "smem"
+        bytes_per_move = 12 * z + 12 + 2 * 8 + 8 + 4 + 12 * acc_rate
+        peak, _ = rw.measure_smem_bandwidth(stream)
+        peak_source = "measured live: conflict-free 16-byte shared-memory loads on every SM"
+    else:
+        bound = "hbm"
+        bytes_per_move = 12 * z + 12 + 12 * acc_rate
+        peak, peak_source = hbm_peak()
+    achieved = bytes_per_move * S * workload["exchange_interval"] / (walk_avg_ms * 1e-3)
     nsh = len(workload["J"])
     if not pipelined:
         kernel = f"walker_kernel<false,{in_smem}>"
@@ -575,14 +606,14 @@ def main():
                        "group_size": sim.info()["group_size"], "accept_rate": acc_rate,
                        "recompute_rate": rec_rate, "conflict_entries": sim.info()["conflict_entries"],
                        "autotune": tune},
-            "roofline": {"bound": "smem", "achieved": achieved / 1e9, "peak": smem_peak / 1e9, "unit": "GB/s",
-                         "frac": achieved / smem_peak, "traffic": traffic,
+            "roofline": {"bound": bound, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": kernel, "bytes_per_move": bytes_per_move,
                          "walker_ms_per_launch": walk_avg_ms, "walker_share_of_step": walker_share,
                          "cycles_per_move_per_walker": walk_avg_ms * 1e-3 * (clk.get("sm_mhz") or 0) * 1e6
                                                        / workload["exchange_interval"],
                          "sms_used": min(S, torch.cuda.get_device_properties(dev).multi_processor_count),
-                         "peak_source": "measured live: conflict-free 16-byte shared-memory loads on every SM"},
+                         "peak_source": peak_source},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (3 * I + 2),
             "clocks": clk,
