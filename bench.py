@@ -362,6 +362,26 @@ def run_batch64(args):
     total_ms = all_max(sum(step_ms), world)
     value = aggregate_rate(moves_per_step * args.steps, world, total_ms)
     info = batch.info()
+
+    # end to end through the public API with host buffers: every job's ln g in (a warm start at
+    # ln f = 1), the batch's intervals, every job's merged ln g out
+    lng_in = [np.zeros(j.B) for j in jobs]
+    h2d = sum(j.n_slots * j.W * 8 + 2 * j.n_slots * 8 for j in jobs)
+    d2h = sum(j.B * 8 for j in jobs)
+    e2e_ms = []
+    for k in range(max(2, args.steps)):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j, lng in zip(jobs, lng_in):
+            j.set_initial_lng(lng, 1.0)
+        batch.run_intervals(I)
+        for j in jobs:
+            j.merge()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = all_max(sum(e2e_ms), world)
+    e2e_value = moves_per_step * len(e2e_ms) * world / (e2e_total * 1e-3)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -374,6 +394,7 @@ def run_batch64(args):
                        "walker_slots": S, "intervals_per_step": I, "moves_per_step": moves_per_step * world,
                        "l2": "flushed between steps (256 MB write)", "graph": True,
                        "tuning": tune, "batch": info, "setup_s": setup_s},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * I * 3,
             "clocks": clk,
         }

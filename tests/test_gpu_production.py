@@ -143,6 +143,37 @@ def test_large_four_shell_geometry_global_path():
     g.close()
 
 
+@pytest.mark.parametrize("placement", ["shared", "global"])
+def test_production_spins_read_back_as_the_device_holds_them(placement):
+    """Production spins live on the device as (x, y, z, 0) FP32 quads, copied into shared-memory
+    planes by the walker when the lattice fits there (placement "global" keeps it in place through a
+    one-job batch).  rewl_get_spins returns FP64 planes [R][3][N]: they start along +z, stay unit
+    vectors, and the energy computed on the host from them and the library's neighbour table equals
+    the device's own recomputation for every configuration."""
+    g = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, L=6, J=(1.0, 0.5, 0.1), n_bins=300, n_windows=3,
+                walkers_per_window=2, seed=4, exchange_interval=3000, group_size=1)
+    sp0 = g.spins()
+    assert np.all(sp0[:, 2] == 1.0) and not sp0[:, :2].any()
+    if placement == "shared":
+        assert g.info()["lattice_in_shared"] == 1
+        g.run_intervals(2)
+    else:
+        with rw.Batch([g]) as b:
+            b.set_tuning(1, 0)
+            assert b.info()["n_smem_lattice_jobs"] == 0
+            b.run_intervals(2)
+    sp = g.spins()
+    assert np.abs(sp[:, :2]).max() > 0.5
+    assert np.allclose(np.linalg.norm(sp, axis=1), 1.0, atol=1e-6)
+    nbr, J = g.neighbours()
+    E_dev = g.replica_energies()
+    for r in range(g.n_slots):
+        S = sp[r]
+        E_host = -0.5 * np.sum(J * np.einsum("cn,czn->zn", S, S[:, nbr]))
+        assert E_host == pytest.approx(E_dev[r], abs=1e-3)
+    g.close()
+
+
 def test_initial_drive_cap_reports_timeout():
     g = rw.REWL(kind=rw.BCC, L=4, J=(1.0, 0.5), n_bins=200, n_windows=4, walkers_per_window=2,
                 init_max_moves=3, mode=rw.TRAJECTORY)
