@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--intervals", type=int, default=20, help="exchange intervals per step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--warm-l", type=int, default=12,
+                   help="warmstart: bcc L of the held-out evaluation jobs (windows about 216 bins wide)")
     p.add_argument("--jobs-per-size", type=int, default=16,
                    help="batch64: jobs per lattice size (16 gives the 64-job workload; smaller for profiling)")
     p.add_argument("--workload", default="single",
@@ -409,8 +411,9 @@ def run_warmstart(args):
     """Time to converged ln g with and without the learned warm start.  Corpus: 192 converged REWL
     runs (bcc L = 4, 5, 6 x 64 random three-shell coupling sets, ln f -> 1e-4) on the restricted
     range [0.6 E_gs, 0] with one bin per spin; the network is trained on them by the library's
-    kernels; evaluation: 4 held-out coupling sets at bcc L = 8 (1024 spins, 16 windows x 2 walkers,
-    ln f -> 1e-5), 2 cold and 2 warm replicas each, cold and warm converged in separate timed batches."""
+    kernels; evaluation: 4 held-out coupling sets at bcc L = --warm-l (default 12: 3456 spins, 61
+    windows x 2 walkers, ln f -> 1e-5), 2 cold and 2 warm replicas each, cold and warm converged in
+    separate timed batches."""
     import numpy as np
     import torch
     from paper_1411_4212_gb300 import warmstart, workloads
@@ -424,7 +427,11 @@ def run_warmstart(args):
     net, hist = warmstart.train(x, t, off, steps=4000, lr=2e-3)
     t2 = time.perf_counter()
     held = [workloads.random_couplings(20_000 + i) for i in range(4)]
-    ok, res, wall = warmstart.warm_vs_cold(net, 8, held, lnf_final=1e-5, replicas=2, separate=True)
+    L = args.warm_l
+    ok, res, wall = warmstart.warm_vs_cold(net, L, held, lnf_final=1e-5, replicas=2, separate=True)
+    probe = warmstart.restricted_job(L, held[0], seed=1, lnf_final=1e-5)
+    h, W = probe.h, probe.W
+    probe.close()
     cold = float(np.mean([m for r in res for m in r["cold_moves"]]))
     warm = float(np.mean([m for r in res for m in r["warm_moves"]]))
     # Monte Carlo time: trial moves per walker until a job has converged, averaged over the jobs.
@@ -433,9 +440,9 @@ def run_warmstart(args):
     line = {
         "metric": "Monte Carlo time (moves per walker) to converged ln g, warm start / plain", "value": warm / cold,
         "unit": "ratio", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
-        "config": {"workload": "warm start: corpus 192 runs bcc L=4,5,6 (ln f->1e-4), evaluation 4 held-out "
-                               "coupling sets at bcc L=8, 16 windows x 2 walkers, ln f->1e-5, range [0.6 E_gs, 0], "
-                               "one bin per spin, ln f0 = 2^-7 (warm) vs 1 (plain)",
+        "config": {"workload": f"warm start: corpus 192 runs bcc L=4,5,6 (ln f->1e-4), evaluation 4 held-out "
+                               f"coupling sets at bcc L={L}, {h} windows x 2 walkers ({W} bins each), ln f->1e-5, "
+                               "range [0.6 E_gs, 0], one bin per spin, ln f0 = 2^-7 (warm) vs 1 (plain)",
                    "converged": bool(ok and meta["converged"])},
         "wall_s": {"plain": wall[0], "warm": wall[1], "ratio": wall[1] / wall[0], "corpus": t1 - t0,
                    "training": t2 - t1, "note": "each group's slowest job of 8"},

@@ -15,6 +15,16 @@ from . import REWL, Batch, Mlp, BCC, PRODUCTION, mlp_features
 from . import workloads
 
 WINDOWS = {4: 4, 5: 6, 6: 8, 7: 12, 8: 16}
+WINDOW_BINS = 216   # window width of the L = 8 layout, kept for larger lattices
+
+
+def windows_for(L, overlap=0.75):
+    """Window count of the restricted range at bcc L: the table above up to L = 8, beyond it as many
+    windows as keep each about WINDOW_BINS wide (h from W = B / (1 + (h - 1)(1 - overlap)))."""
+    if L in WINDOWS:
+        return WINDOWS[L]
+    N = 2 * L ** 3
+    return max(2, int(round(1 + (N / WINDOW_BINS - 1) / (1 - overlap))))
 # input normalisation x' = (x - SHIFT) * SCALE of (E/N, 1/L, J1, J2, J3, J4)
 SHIFT = np.array([-1.9, 0.19, 1.0, 0.4, 0.0, 0.0], dtype=np.float32)
 SCALE = np.array([1 / 1.1, 20.0, 1.0, 5.0, 10.0, 1.0], dtype=np.float32)
@@ -32,7 +42,7 @@ def ground_state(L, J):
 def restricted_job(L, J, seed, lnf_final, walkers=2, exchange_interval=4000, stream=None):
     N = 2 * L ** 3
     return REWL(kind=BCC, mode=PRODUCTION, L=L, J=J, e_min=0.6 * ground_state(L, J), e_max=0.0, n_bins=N,
-                n_windows=WINDOWS[L], walkers_per_window=walkers, overlap=0.75, flatness=0.8, lnf_final=lnf_final,
+                n_windows=windows_for(L), walkers_per_window=walkers, overlap=0.75, flatness=0.8, lnf_final=lnf_final,
                 seed=seed, exchange_interval=exchange_interval, group_size=1, stream=stream)
 
 
