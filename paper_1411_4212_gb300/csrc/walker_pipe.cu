@@ -897,9 +897,11 @@ __global__ void __launch_bounds__(kWalkerThreads, 1) walker_pipe_kernel(const Wa
 // The same over a lattice in global memory, with the arguments read from a device copy (through
 // L1) and the per-launch moves and recompute flag as parameters.  On GB300 the bcc L = 32
 // four-shell walker ran 25 % faster this way than with parameter arguments, while the
-// shared-memory walker ran 3 % slower, so each keeps its own form.
+// shared-memory walker ran 3 % slower, so each keeps its own form.  Register budget: four blocks
+// per SM (128 registers), the residency that runs 512 walkers in one wave at 2048-entry tables;
+// 4 % faster than the default budget (96 registers).
 template <bool kTraj, int NSH>
-__global__ void __launch_bounds__(kWalkerThreads)
+__global__ void __launch_bounds__(kWalkerThreads, 4)
     walker_pipe_global_kernel(const WalkerArgs* __restrict__ ap, long long moves, int recompute) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[kWalkerThreads / 32];
@@ -910,8 +912,12 @@ __global__ void __launch_bounds__(kWalkerThreads)
 // (job, slot) items from the work list until it is exhausted; a CTA holds `workers` workers, each
 // with its own shared-memory arena and barriers (1 + 5w .. 5 + 5w).  A job's lattice sits in the
 // arena or stays in global memory (L2) as its smem_lattice flag says.
+// Register budget: at least two blocks of the largest shape per SM (at most 170 registers per
+// thread).  The tunings the autotuner picks are limited by shared memory, not registers; on GB300
+// the 64-job batch ran 7 % faster at this budget (168 registers, no spills) than at the default
+// (96 registers and a spill) and 3 % faster than with the budget fully open.
 template <bool kTraj, int NSH>
-__global__ void __launch_bounds__(kBatchMaxWorkers * kWorkerThreads)
+__global__ void __launch_bounds__(kBatchMaxWorkers * kWorkerThreads, 2)
     walker_batch_kernel(const WalkerArgs* __restrict__ jobs, const int2* __restrict__ items, int n_items, int* head,
                         long long moves, int recompute, unsigned arena) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
