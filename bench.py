@@ -413,7 +413,7 @@ def run_warmstart(args):
     range [0.6 E_gs, 0] with one bin per spin; the network is trained on them by the library's
     kernels; evaluation: 4 held-out coupling sets at bcc L = --warm-l (default 12: 3456 spins, 61
     windows x 2 walkers, ln f -> 1e-5), 2 cold and 2 warm replicas each, cold and warm converged in
-    separate timed batches."""
+    separate timed batches, each autotuned first."""
     import numpy as np
     import torch
     from paper_1411_4212_gb300 import warmstart, workloads
@@ -428,7 +428,7 @@ def run_warmstart(args):
     t2 = time.perf_counter()
     held = [workloads.random_couplings(20_000 + i) for i in range(4)]
     L = args.warm_l
-    ok, res, wall = warmstart.warm_vs_cold(net, L, held, lnf_final=1e-5, replicas=2, separate=True)
+    ok, res, wall = warmstart.warm_vs_cold(net, L, held, lnf_final=1e-5, replicas=2, separate=True, autotune=True)
     probe = warmstart.restricted_job(L, held[0], seed=1, lnf_final=1e-5)
     h, W = probe.h, probe.W
     probe.close()

@@ -88,14 +88,16 @@ def centred_rms(a, b):
     return float(np.sqrt(np.mean((d - d.mean()) ** 2)))
 
 
-def warm_vs_cold(net, L, couplings, lnf_final=1e-5, replicas=2, lnf0=LNF0_WARM, seed0=900, separate=False):
+def warm_vs_cold(net, L, couplings, lnf_final=1e-5, replicas=2, lnf0=LNF0_WARM, seed0=900, separate=False,
+                 autotune=False):
     """For every coupling set: `replicas` cold starts (ln g = 0, ln f0 = 1) and `replicas` warm starts
     (network ln g, ln f0).  Returns (converged, per-set records, wall seconds).  Records hold the moves
     per walker to converge and the centred rms of each converged ln g against the first cold
     replica; a job's walkers all walk until the whole job has converged, so its moves per walker are
     the job's time to converge.  separate=False converges all jobs in one batch (wall = None);
     separate=True converges the cold jobs, then the warm jobs (network inference included), in two
-    timed batches: wall = (cold seconds, warm seconds)."""
+    timed batches: wall = (cold seconds, warm seconds).  autotune=True lets each batch's autotuner
+    pick its launch shape first (its trial moves are ordinary moves of the jobs)."""
     import time
     cold, warm, pred = [], [], []
     s = seed0
@@ -117,15 +119,15 @@ def warm_vs_cold(net, L, couplings, lnf_final=1e-5, replicas=2, lnf0=LNF0_WARM, 
     flat_warm = [j for group in warm for j in group]
     if separate:
         t0 = time.perf_counter()
-        ok = converge(flat_cold, autotune=False)
+        ok = converge(flat_cold, autotune=autotune)
         t1 = time.perf_counter()
         start_warm()
-        ok = converge(flat_warm, autotune=False) and ok
+        ok = converge(flat_warm, autotune=autotune) and ok
         t2 = time.perf_counter()
         wall = (t1 - t0, t2 - t1)
     else:
         start_warm()
-        ok = converge(flat_cold + flat_warm, autotune=False)
+        ok = converge(flat_cold + flat_warm, autotune=autotune)
         wall = None
     out = []
     for J, cs, ws, p in zip(couplings, cold, warm, pred):
