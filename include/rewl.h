@@ -180,9 +180,10 @@ rewl_status rewl_walk(rewl_handle* h);
 rewl_status rewl_flatness(rewl_handle* h);
 
 /* Conflict-table autotuner of the pipelined walker with the lattice in global memory (rewl_info
- * .pipelined = 1, .lattice_in_shared = 0): times one walker launch of trial_moves (> 0) moves per
- * walker for each table of 8192 down to 512 entries (at most one per site), twice (the second round
- * in reverse order), and keeps the table with the fastest trial.
+ * .pipelined = 1, .lattice_in_shared = 0).  The paper has no counterpart: the moves it times are
+ * those of Sec. 4.2 (Eq. 4); only the launch shape changes.  Times one walker launch of
+ * trial_moves (> 0) moves per walker for each table of 8192 down to 512 entries (at most one per
+ * site), twice (the second round in reverse order), and keeps the table with the fastest trial.
  * A smaller table leaves more shared memory to L1 and fits more walkers per SM; sites sharing an
  * entry cost extra exact corrections, never a different result.  The default is 2048 entries.
  * Other handles have nothing to tune: their table stays and no move is made.  The timed moves are
