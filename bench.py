@@ -1,16 +1,19 @@
 """Benchmark: spin-move attempts/s of replica-exchange Wang-Landau on one GB300.
 
-Workload (the paper's method at the benchmark geometry): classical Heisenberg model on bcc L=16
-(8192 spins, periodic), couplings J1=1 (8 nn), J2=0.5 (6 nnn), energy range [E_gs, 0] in 2000 bins,
-16 windows x 4 walkers at 75 % overlap, flatness 0.8, ln f 1 -> 1e-8, exchange every 1e4 moves;
-production mode (FP32 spins and dE, 64-bit fixed-point ln g and energy).  Synthetic: the state is
-the sampler's own, started from the aligned configuration and driven into the windows (untimed).
+Default workload (the paper's method on the large configuration): classical Heisenberg model on bcc
+L=32 (65536 spins, periodic), four coupling shells J=(1, 0.6, -0.05, -0.1) (8+6+12+24 = 50
+neighbours), energy range [E_gs, 0] in 8000 bins, 64 windows x 8 walkers at 75 % overlap, flatness
+0.8, ln f 1 -> 1e-8, exchange every 1e4 moves; production mode (FP32 spins and dE, 64-bit
+fixed-point ln g and energy).  Synthetic: the state is the sampler's own, started from the aligned
+configuration and driven into the windows (untimed).  --workload cfg2 runs bcc L=16 with two shells,
+16 windows x 4 walkers and 2000 bins instead.
 
 One step = `intervals` exchange intervals, each = walker kernel (1e4 trial moves per walker,
-energy recomputation) + replica-exchange kernel + flatness kernel, then the merge kernels (all steps
-of the hot path).  The L2 cache is flushed (256 MB write) between timed steps.
+energy recomputation every 8th) + replica-exchange kernel + flatness kernel, then the merge kernels
+(all steps of the hot path).  The L2 cache is flushed (256 MB write) between timed steps; the bcc L=32
+lattices alone hold 537 MB.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
 
 With N > 1 (torchrun) every rank runs an independent replica of the workload with its own seed
 (weak scaling, no data-path collective); rank 0 prints the aggregate.
@@ -30,14 +33,16 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(L=16, J=(1.0, 0.5), n_bins=2000, n_windows=16, walkers_per_window=4, overlap=0.75,
-                flatness=0.8, lnf_final=1e-8, exchange_interval=10000)
-WORKLOAD_NAME = ("REWL bcc L=16 (8192 spins) J1=1 J2=0.5, [E_gs,0] 2000 bins, 16 windows x 4 walkers, "
-                 "75% overlap, exchange every 1e4 moves")
 LARGE = dict(L=32, J=(1.0, 0.6, -0.05, -0.1), n_bins=8000, n_windows=64, walkers_per_window=8, overlap=0.75,
              flatness=0.8, lnf_final=1e-8, exchange_interval=10000)
 LARGE_NAME = ("REWL bcc L=32 (65536 spins) J=(1,0.6,-0.05,-0.1) (50 neighbours), [E_gs,0] 8000 bins, "
               "64 windows x 8 walkers, 75% overlap, exchange every 1e4 moves")
+CFG2 = dict(L=16, J=(1.0, 0.5), n_bins=2000, n_windows=16, walkers_per_window=4, overlap=0.75,
+            flatness=0.8, lnf_final=1e-8, exchange_interval=10000)
+CFG2_NAME = ("REWL bcc L=16 (8192 spins) J1=1 J2=0.5, [E_gs,0] 2000 bins, 16 windows x 4 walkers, "
+             "75% overlap, exchange every 1e4 moves")
+# workload -> (configuration, name, walkers per window of the bounded CPU sample)
+WORKLOADS = {"large": (LARGE, LARGE_NAME, 1), "cfg2": (CFG2, CFG2_NAME, 4)}
 METRIC = "spin-move attempts/s"
 UNIT = "moves/s"
 
@@ -55,12 +60,12 @@ def parse():
                    help="warmstart: bcc L of the held-out evaluation jobs (windows about 216 bins wide)")
     p.add_argument("--jobs-per-size", type=int, default=16,
                    help="batch64: jobs per lattice size (16 gives the 64-job workload; smaller for profiling)")
-    p.add_argument("--workload", default="single",
-                   choices=["single", "large", "batch64", "warmstart", "weak-scaling"],
-                   help="single: one job, bcc L=16 (the headline line); large: one job, bcc L=32 with four "
-                        "shells, 64 windows x 8 walkers; batch64: 64 jobs of bcc L=8..20 "
-                        "in one persistent launch; warmstart: learned warm start versus plain REWL; "
-                        "weak-scaling: moves to finish the first WL iteration versus L")
+    p.add_argument("--workload", default="large",
+                   choices=["large", "cfg2", "batch64", "warmstart", "weak-scaling"],
+                   help="large: one job, bcc L=32 with four shells, 64 windows x 8 walkers (the headline "
+                        "line); cfg2: one job, bcc L=16 with two shells, 16 windows x 4 walkers; batch64: 64 "
+                        "jobs of bcc L=8..20 in one persistent launch; warmstart: learned warm start versus "
+                        "plain REWL; weak-scaling: moves to finish the first WL iteration versus L")
     return p.parse_args()
 
 
@@ -170,91 +175,116 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands on the host cores
 # ------------------------------------------------------------------------------------------------
-def oracle_rate(seconds, seed=1, min_intervals=1):
+def cpu_sample(workload):
+    """The bounded CPU sample of a workload: its lattice, couplings, bins and window layout, with
+    `sample_m` walkers per window instead of all of them (moves/s per walker do not depend on m)."""
+    cfg, name, sample_m = WORKLOADS[workload]
+    return dict(cfg, walkers_per_window=sample_m), name
+
+
+def oracle_interval(s, cfg):
+    """One exchange interval of the oracle as it stands, the steps of the hot path: Wang-Landau moves of
+    every walker, one replica-exchange round, the flatness test.  (The oracle's own interval also
+    recomputes every walker's energy from scratch as a drift check, which changes no state; at z = 50
+    it costs three times the moves, so it is left out here.)"""
+    s.run_moves_only(cfg["exchange_interval"])
+    s.exchange()
+    s.flatness()
+    return s.n_slots * cfg["exchange_interval"]
+
+
+def _oracle_replica(workload, seed):
     import oracle
-    s = oracle.OracleREWL(kind=oracle.BCC, seed=seed, **WORKLOAD)
+    cfg, _ = cpu_sample(workload)
+    s = oracle.OracleREWL(kind=oracle.BCC, seed=seed, **cfg)
     s.init_walkers()
-    moves = 0
+    return s, cfg
+
+
+def _oracle_rate_worker(args):
+    seconds, seed, workload = args
+    s, cfg = _oracle_replica(workload, seed)
+    moves = n = 0
     t0 = time.perf_counter()
-    n = 0
-    while True:
-        s.run_intervals(1)
+    while n < 1 or time.perf_counter() - t0 < seconds:
+        moves += oracle_interval(s, cfg)
         n += 1
-        moves += s.n_slots * WORKLOAD["exchange_interval"]
-        if n >= min_intervals and time.perf_counter() - t0 >= seconds:
-            break
     dt = time.perf_counter() - t0
     return moves / dt, moves, dt, n
 
 
-def _oracle_rate_worker(args):
-    seconds, seed = args
-    return oracle_rate(seconds, seed=seed)
-
-
-def cpu_baseline(seconds):
-    """The single-threaded oracle as it stands, one independent replica of the workload (own seed)
-    per host core, in spawned processes; the value is the replicas' aggregate rate."""
-    import multiprocessing as mp
+def host_cores():
     try:
         cores = len(os.sched_getaffinity(0))
     except AttributeError:
         cores = os.cpu_count() or 1
-    cores = max(1, min(cores, 64))
+    return max(1, min(cores, 64))
+
+
+def cpu_baseline(seconds, workload):
+    """The single-threaded oracle as it stands, one independent replica of the bounded sample (own seed)
+    per host core, in spawned processes; the value is the replicas' aggregate rate."""
+    import multiprocessing as mp
+    cores = host_cores()
+    cfg, _ = cpu_sample(workload)
     with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(_oracle_rate_worker, [(seconds, 1 + i) for i in range(cores)])
+        res = pool.map(_oracle_rate_worker, [(seconds, 1 + i, workload) for i in range(cores)])
     rate = sum(r[0] for r in res)
     moves = sum(r[1] for r in res)
     n = sum(r[3] for r in res)
     dt = max(r[2] for r in res)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "single_core_value": res[0][0],
-            "sample": f"{cores} independent replicas of the same workload, one per core, {n} exchange intervals in all "
-                      f"({moves} trial moves incl. energy check, exchange, flatness) in {dt:.1f} s, FP64"}
+            "sample": f"{cores} independent replicas, one per core, of the same lattice, couplings, bins and "
+                      f"{cfg['n_windows']} windows with {cfg['walkers_per_window']} walker(s) per window; {n} exchange "
+                      f"intervals in all ({moves} trial moves with the exchange rounds and flatness tests) in "
+                      f"{dt:.1f} s, FP64"}
 
 
 # ------------------------------------------------------------------------------------------------
 # reference arm: the oracle timed as it stands, step by step
 # ------------------------------------------------------------------------------------------------
 def _reference_worker(args):
-    steps, warmup, seed = args
-    import oracle
-    s = oracle.OracleREWL(kind=oracle.BCC, seed=seed, **WORKLOAD)
-    s.init_walkers()
+    steps, warmup, seed, workload = args
+    s, cfg = _oracle_replica(workload, seed)
     for _ in range(warmup):
-        s.run_intervals(1)
+        oracle_interval(s, cfg)
+    moves = 0
     t0 = time.perf_counter()
     for _ in range(steps):
-        s.run_intervals(1)
-    return s.n_slots * WORKLOAD["exchange_interval"] * steps, time.perf_counter() - t0
+        moves += oracle_interval(s, cfg)
+    return moves, time.perf_counter() - t0
 
 
 def run_reference(args):
-    """The FP64 oracle as it stands, one independent replica of the workload per host core (spawned
-    processes); a step is one exchange interval of every replica."""
+    """The FP64 oracle as it stands, one independent replica of the bounded sample per host core
+    (spawned processes); a step is one exchange interval of every replica."""
     import multiprocessing as mp
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    try:
-        cores = len(os.sched_getaffinity(0))
-    except AttributeError:
-        cores = os.cpu_count() or 1
-    cores = max(1, min(cores, 64))
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm covers the single-job workloads "
+                                                              f"({', '.join(WORKLOADS)}), not {args.workload}"}))
+        return 0
+    cores = host_cores()
+    cfg, name = cpu_sample(args.workload)
     with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(_reference_worker, [(args.steps, args.warmup, 1 + i) for i in range(cores)])
+        res = pool.map(_reference_worker, [(args.steps, args.warmup, 1 + i, args.workload) for i in range(cores)])
     moves = sum(r[0] for r in res)
     dt = max(r[1] for r in res)
     value = moves / dt
+    sample = (f"{args.steps} exchange intervals of {cores} independent replicas, one per host core, each with the "
+              f"lattice, couplings, bins and {cfg['n_windows']} windows of the workload and {cfg['walkers_per_window']} "
+              f"walker(s) per window ({moves} moves in all)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME,
-                   "step": f"one exchange interval of each of {cores} FP64 oracle replicas, one per host core"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} exchange intervals of {cores} independent replicas "
-                                   f"({moves} moves in all)"},
+        "config": {"workload": name,
+                   "step": f"one exchange interval (moves, exchange round, flatness test) of each of {cores} FP64 "
+                           "oracle replicas, one per host core"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -520,7 +550,7 @@ def main():
     stream = torch.cuda.current_stream()
     I = args.intervals
 
-    workload, workload_name = (LARGE, LARGE_NAME) if args.workload == "large" else (WORKLOAD, WORKLOAD_NAME)
+    workload, workload_name, _ = WORKLOADS[args.workload]
     sim = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, seed=replica_seed(rank), stream=stream, **workload)
     sim.init_walkers()
     # lattices in global memory: the conflict-table size is timed before the warm-up (ordinary moves)
@@ -619,8 +649,8 @@ def main():
     e2e_value = moves_per_step * len(e2e_ms) * world / (e2e_total * 1e-3)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and args.gpus == 1 and args.workload == "single":
-        cpu = cpu_baseline(args.cpu_seconds)
+    if rank == 0 and not args.no_cpu_baseline and args.gpus == 1:
+        cpu = cpu_baseline(args.cpu_seconds, args.workload)
 
     if rank == 0:
         line = {

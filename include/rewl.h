@@ -105,7 +105,20 @@ typedef struct {
   double lnf_initial;            /* initial ln f; 0 = 1 (f0 = e, Sec. 4.2) */
   double timeout_s;              /* wall-clock cap for rewl_run_stage (0 = none) */
   void* cuda_stream;             /* cudaStream_t used for every launch (NULL = default stream) */
+  int32_t resolver;              /* production mode, warp-specialised walker: how each batch of 32
+                                    trial moves is resolved in order.  REWL_RESOLVER_AUTO (0) picks
+                                    per batch from the previous batch's event counts; the others
+                                    force one path for every batch.  All paths take the same
+                                    decisions (same state, bit for bit); only their cost differs */
 } rewl_config;
+
+enum {
+  REWL_RESOLVER_AUTO = 0,       /* per batch: the cheapest of the three for the last batch's events */
+  REWL_RESOLVER_SCAN = 1,       /* one 64-bit warp prefix scan of the energy increments, one ballot
+                                   round per event (bin change, correction) */
+  REWL_RESOLVER_BLOCKS = 2,     /* branch-free blocks of 8 moves; events leave the block */
+  REWL_RESOLVER_SEQUENTIAL = 3  /* one move at a time */
+};
 
 typedef struct {
   int64_t moves;               /* trial moves attempted in the call (all walkers) */
@@ -141,6 +154,9 @@ typedef struct {
   int64_t accepts;
   int64_t recomputes;          /* trial moves whose dE was re-evaluated after an earlier accepted
                                   move in the same batch touched its neighbourhood */
+  int64_t batches_scan;        /* production, warp-specialised walker: batches of 32 moves resolved */
+  int64_t batches_blocks;      /*   by the warp scan, by 8-move blocks and one move at a time */
+  int64_t batches_sequential;  /*   (all 0 for the other walkers and in trajectory mode) */
 } rewl_counters;
 
 /* Create a simulation: lattice and couplings (Sec. 3), windows (Sec. 4.3), m walkers per window,
@@ -242,6 +258,14 @@ rewl_status rewl_stitch_device_noalloc(const double* frag, const int32_t* starts
 rewl_status rewl_thermo(const double* lng, const double* e_centres, int n_bins, double n_spins,
                         const double* T, int n_T, double* U_out, double* C_out, double* lnZ_out,
                         void* cuda_stream);
+
+/* Temperature of the specific-heat maximum (the paper reads the transition temperature off this peak,
+ * Sec. 5; C(T) from Sec. 4.1, Eq. 3): the grid argmax b of C (lowest index on ties), refined by the
+ * vertex of the parabola through (T, C) at b-1, b, b+1, i.e. T_b + (dT/2) (C_{b-1} - C_{b+1}) /
+ * (C_{b-1} - 2 C_b + C_{b+1}) with dT = T_{b+1} - T_b (a uniform grid); at either end of the grid, or
+ * when the denominator is 0, T_b.  T, C: host [n_T] (e.g. from rewl_thermo), increasing T; T_peak:
+ * host, one double.  Computed on the device on cuda_stream; REWL_EINVAL for NULL or n_T < 1. */
+rewl_status rewl_peak_temperature(const double* T, const double* C, int n_T, double* T_peak, void* cuda_stream);
 
 /* Replace every walker's ln g by lng (host, [n_bins] over the global bins; each walker takes its
  * window's slice) and set ln f = lnf0 (> 0) for all walkers; histograms are cleared. */

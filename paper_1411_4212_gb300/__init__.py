@@ -16,8 +16,8 @@ import os
 
 import numpy as np
 
-__all__ = ["REWL", "Batch", "Mlp", "RewlError", "load_library", "thermo", "stitch_device", "device_exp",
-           "measure_smem_bandwidth", "BCC", "CHAIN", "TABLE", "PRODUCTION", "TRAJECTORY"]
+__all__ = ["REWL", "Batch", "Mlp", "RewlError", "load_library", "thermo", "peak_temperature", "stitch_device",
+           "device_exp", "measure_smem_bandwidth", "BCC", "CHAIN", "TABLE", "PRODUCTION", "TRAJECTORY"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librewl.so")
@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(HERE, "librewl.so")
 BCC, CHAIN, TABLE = 0, 1, 2
 ITERATION_WALKER, ITERATION_WINDOW = 0, 1
 PRODUCTION, TRAJECTORY = 0, 1
+RESOLVER_AUTO, RESOLVER_SCAN, RESOLVER_BLOCKS, RESOLVER_SEQUENTIAL = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
 _STATUS = {0: "REWL_OK", 1: "REWL_EINVAL", 2: "REWL_ENOMEM", 3: "REWL_ECUDA", 4: "REWL_ETIMEOUT",
            5: "REWL_ESTATE"}
@@ -54,7 +55,8 @@ class Config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("mode", C.c_int32), ("group_size", C.c_int32),
                 ("exchange_interval", C.c_int64), ("max_moves_per_stage", C.c_int64),
                 ("init_max_moves", C.c_int64), ("recompute_every", C.c_int32), ("iteration", C.c_int32),
-                ("lnf_initial", C.c_double), ("timeout_s", C.c_double), ("cuda_stream", C.c_void_p)]
+                ("lnf_initial", C.c_double), ("timeout_s", C.c_double), ("cuda_stream", C.c_void_p),
+                ("resolver", C.c_int32)]
 
 
 class StageStats(C.Structure):
@@ -97,7 +99,11 @@ class BatchInfo(C.Structure):
 
 
 class Counters(C.Structure):
-    _fields_ = [("moves", C.c_int64), ("accepts", C.c_int64), ("recomputes", C.c_int64)]
+    _fields_ = [("moves", C.c_int64), ("accepts", C.c_int64), ("recomputes", C.c_int64),
+                ("batches_scan", C.c_int64), ("batches_blocks", C.c_int64), ("batches_sequential", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -134,6 +140,7 @@ def load_library(path=LIB_PATH):
         "rewl_stitch_device_noalloc": ([_vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp], st),
         "rewl_thermo": ([_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, _vp, _vp, _vp], st),
         "rewl_set_initial_lng": ([_vp, _vp, C.c_double], st),
+        "rewl_peak_temperature": ([_vp, _vp, C.c_int, C.POINTER(C.c_double), _vp], st),
         "rewl_get_info": ([_vp, C.POINTER(Info)], st),
         "rewl_get_walkers": ([_vp] + [_vp] * 10, st),
         "rewl_get_spins": ([_vp, _vp], st),
@@ -197,14 +204,16 @@ class REWL:
 
     kind: BCC (L cells per side, couplings per shell J[0..3]), CHAIN (L spins, J[0]) or TABLE
     (nbr, Jt arrays [z][n_sites]).  mode: PRODUCTION (FP32 spins, fixed-point ln g / energy) or
-    TRAJECTORY (FP64, bit-reproducible walk).
+    TRAJECTORY (FP64, bit-reproducible walk).  resolver: RESOLVER_AUTO, or one of RESOLVER_SCAN /
+    _BLOCKS / _SEQUENTIAL forced for every batch of the production pipelined walker (the same
+    decisions at a different cost).
     """
 
     def __init__(self, kind=BCC, L=4, J=(1.0, 0.5), nbr=None, Jt=None, e_min=math.nan, e_max=math.nan,
                  n_bins=200, n_windows=4, walkers_per_window=2, overlap=0.75, flatness=0.8,
                  lnf_final=1e-3, seed=1, mode=PRODUCTION, group_size=0, exchange_interval=10000,
                  max_moves_per_stage=0, init_max_moves=0, recompute_every=0, lnf_initial=0.0,
-                 timeout_s=0.0, stream=None, iteration=0):
+                 timeout_s=0.0, stream=None, iteration=0, resolver=RESOLVER_AUTO):
         lib = load_library()
         lat = Lattice()
         lat.kind = kind
@@ -236,6 +245,7 @@ class REWL:
         cfg.lnf_initial = lnf_initial
         cfg.timeout_s = timeout_s
         cfg.cuda_stream = _stream_ptr(stream)
+        cfg.resolver = resolver
         h = _vp()
         _check(lib.rewl_create(C.byref(lat), C.byref(cp), C.byref(win), walkers_per_window, overlap, flatness,
                                lnf_final, C.byref(cfg), C.byref(h)))
@@ -324,11 +334,13 @@ class REWL:
         _check(self._lib.rewl_set_initial_lng(self._h, _ptr(lng), float(lnf0)), self._h)
 
     def run_to_convergence(self, max_stages=1000):
+        """Stages (rewl_run_stage) until every walker has ln f < lnf_final.  Stops at the first stage
+        that a cap (max_moves_per_stage, timeout_s) ended: that stage's dict has capped = True."""
         stages = []
         for _ in range(max_stages):
             st = self.run_stage()
             stages.append(st)
-            if st["all_done"]:
+            if st["all_done"] or st["capped"]:
                 break
         return stages
 
@@ -372,7 +384,7 @@ class REWL:
     def counters(self):
         c = Counters()
         _check(self._lib.rewl_get_counters(self._h, C.byref(c)), self._h)
-        return {"moves": c.moves, "accepts": c.accepts, "recomputes": c.recomputes}
+        return c.as_dict()
 
     def neighbours(self):
         nbr = np.zeros((self.z, self.N), dtype=np.int32)
@@ -543,16 +555,14 @@ def thermo(lng, centres, n_spins, T, stream=None):
     return U, Cv, lnZ
 
 
-def peak_temperature(T, Cv):
-    """Grid argmax of C(T) refined by a 3-point parabola (host arithmetic on the kernel's output)."""
-    i = int(np.argmax(Cv))
-    if i == 0 or i == len(T) - 1:
-        return float(T[i])
-    c0, c1, c2 = Cv[i - 1], Cv[i], Cv[i + 1]
-    den = c0 - 2 * c1 + c2
-    if den == 0:
-        return float(T[i])
-    return float(T[i] + 0.5 * (T[i + 1] - T[i]) * (c0 - c2) / den)
+def peak_temperature(T, Cv, stream=None):
+    """Temperature of the maximum of C(T): grid argmax refined by a 3-point parabola (library kernel)."""
+    lib = load_library()
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    Cv = np.ascontiguousarray(Cv, dtype=np.float64)
+    out = C.c_double()
+    _check(lib.rewl_peak_temperature(_ptr(T), _ptr(Cv), T.size, C.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 def stitch_device(frag, starts, n_bins, out, bstar=None, stream=None):

@@ -34,6 +34,7 @@ struct rewl_handle {
   long long exchange_interval = 0, max_moves_per_stage = 0, init_cap = 0;
   int recompute_every = 1;
   bool by_window = false;         // window-synchronous iteration (REWL_ITERATION_WINDOW)
+  int resolver = REWL_RESOLVER_AUTO;
   double timeout_s = 0;
   cudaStream_t stream = nullptr;
   std::vector<int32_t> starts;
@@ -63,6 +64,7 @@ struct rewl_handle {
   long long* d_steps = nullptr;
   long long* d_accepts = nullptr;
   long long* d_recomputes = nullptr;
+  long long* d_path_batches = nullptr;
   long long* d_init_moves = nullptr;
   double* d_drift = nullptr;
   int32_t* d_ctrl = nullptr;
@@ -193,6 +195,7 @@ WalkerState state_of(rewl_handle* h) {
   s.steps = h->d_steps;
   s.accepts = h->d_accepts;
   s.recomputes = h->d_recomputes;
+  s.path_batches = h->d_path_batches;
   s.init_moves = h->d_init_moves;
   s.drift = h->d_drift;
   s.ctrl = h->d_ctrl;
@@ -236,6 +239,7 @@ WalkerArgs walker_args(rewl_handle* h, bool init, bool recompute, long long move
   a.lnf_final = h->lnf_final;
   a.own_mask = h->own_entries > 0 ? h->own_entries - 1 : 0;
   a.smem_lattice = (h->pipe ? h->pipe_smem_lattice : h->smem_lattice) ? 1 : 0;
+  a.resolver = h->resolver;
   return a;
 }
 
@@ -326,6 +330,9 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   if (cfg->iteration != REWL_ITERATION_WALKER && cfg->iteration != REWL_ITERATION_WINDOW)
     return bad("iteration must be REWL_ITERATION_WALKER or REWL_ITERATION_WINDOW");
   h->by_window = cfg->iteration == REWL_ITERATION_WINDOW;
+  if (cfg->resolver < REWL_RESOLVER_AUTO || cfg->resolver > REWL_RESOLVER_SEQUENTIAL)
+    return bad("resolver must be REWL_RESOLVER_AUTO, _SCAN, _BLOCKS or _SEQUENTIAL");
+  h->resolver = cfg->resolver;
   h->timeout_s = cfg->timeout_s;
   h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
   h->ex = exp_coeffs();
@@ -550,6 +557,7 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   A(&h->d_steps, S);
   A(&h->d_accepts, S);
   A(&h->d_recomputes, S);
+  A(&h->d_path_batches, 3 * S);
   A(&h->d_init_moves, S);
   A(&h->d_drift, S);
   A(&h->d_ctrl, 4);
@@ -623,6 +631,7 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   zero(h->d_steps, S * sizeof(long long));
   zero(h->d_accepts, S * sizeof(long long));
   zero(h->d_recomputes, S * sizeof(long long));
+  zero(h->d_path_batches, 3 * S * sizeof(long long));
   zero(h->d_init_moves, S * sizeof(long long));
   zero(h->d_drift, S * sizeof(double));
   zero(h->d_ctrl, 4 * sizeof(int32_t));
@@ -1079,6 +1088,22 @@ rewl_status rewl_thermo(const double* lng, const double* centres, int B, double 
   return REWL_OK;
 }
 
+rewl_status rewl_peak_temperature(const double* T, const double* C, int nT, double* T_peak, void* cuda_stream) {
+  if (!T || !C || !T_peak || nT < 1) return fail(nullptr, REWL_EINVAL, "bad peak arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  double* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, sizeof(double) * (2 * (size_t)nT + 1), st);
+  if (e != cudaSuccess) return fail(nullptr, REWL_ENOMEM, "peak scratch allocation failed");
+  e = cudaMemcpyAsync(d, T, sizeof(double) * nT, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + nT, C, sizeof(double) * nT, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_peak(d, d + nT, nT, d + 2 * nT, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(T_peak, d + 2 * nT, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(nullptr, REWL_ECUDA, std::string("peak: ") + cudaGetErrorString(e));
+  return REWL_OK;
+}
+
 rewl_status rewl_set_initial_lng(rewl_handle* h, const double* lng, double lnf0) {
   rewl_status s = check_ready(h);
   if (s != REWL_OK) return s;
@@ -1232,16 +1257,20 @@ rewl_status rewl_get_counters(rewl_handle* h, rewl_counters* out) {
   if (s != REWL_OK) return s;
   if (!out) return fail(h, REWL_EINVAL, "out is NULL");
   const size_t S = h->S;
-  std::vector<long long> a(S), st(S), r(S);
+  std::vector<long long> a(S), st(S), r(S), pb(3 * S);
   CUDA_TRY(h, cudaMemcpyAsync(a.data(), h->d_accepts, S * 8, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(st.data(), h->d_steps, S * 8, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(r.data(), h->d_recomputes, S * 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(pb.data(), h->d_path_batches, 3 * S * 8, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  out->moves = out->accepts = out->recomputes = 0;
+  std::memset(out, 0, sizeof *out);
   for (size_t i = 0; i < S; ++i) {
     out->moves += st[i];
     out->accepts += a[i];
     out->recomputes += r[i];
+    out->batches_scan += pb[3 * i];
+    out->batches_blocks += pb[3 * i + 1];
+    out->batches_sequential += pb[3 * i + 2];
   }
   return REWL_OK;
 }

@@ -450,6 +450,58 @@ cudaError_t launch_thermo(const double* lng, const double* E, int B, double n_sp
   return cudaGetLastError();
 }
 
+// Temperature of the specific-heat maximum: the grid argmax of C (lowest index on ties), refined by
+// the vertex of the parabola through it and its two neighbours, T_b + (dT/2) (C_{b-1} - C_{b+1}) /
+// (C_{b-1} - 2 C_b + C_{b+1}); at either end of the grid (or for a flat triple) the grid value.  One CTA.
+__global__ void peak_kernel(const double* T, const double* C, int nT, double* out) {
+  __shared__ double bv_s[32];
+  __shared__ int bi_s[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double ninf = __longlong_as_double((long long)0xfff0000000000000ULL);
+  double bv = ninf;
+  int bi = nT;
+  for (int i = threadIdx.x; i < nT; i += blockDim.x)   // increasing i: the first maximum is kept
+    if (bi == nT || C[i] > bv) {
+      bv = C[i];
+      bi = i;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(kFullMask, bv, o);
+    const int oi = __shfl_xor_sync(kFullMask, bi, o);
+    if (oi < nT && (bi == nT || ov > bv || (ov == bv && oi < bi))) {
+      bv = ov;
+      bi = oi;
+    }
+  }
+  if (lane == 0) {
+    bv_s[warp] = bv;
+    bi_s[warp] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (bi_s[w] < nT && (bi == nT || bv_s[w] > bv || (bv_s[w] == bv && bi_s[w] < bi))) {
+        bv = bv_s[w];
+        bi = bi_s[w];
+      }
+    double t = T[bi];
+    if (bi > 0 && bi < nT - 1) {
+      const double c0 = C[bi - 1], c1 = C[bi], c2 = C[bi + 1];
+      const double den = __dadd_rn(__dsub_rn(c0, __dmul_rn(2.0, c1)), c2);
+      if (den != 0.0) {
+        const double dT = __dsub_rn(T[bi + 1], T[bi]);
+        t = __dadd_rn(t, __ddiv_rn(__dmul_rn(__dmul_rn(0.5, dT), __dsub_rn(c0, c2)), den));
+      }
+    }
+    *out = t;
+  }
+}
+
+cudaError_t launch_peak(const double* T, const double* C, int nT, double* out, cudaStream_t stream) {
+  peak_kernel<<<1, 256, 0, stream>>>(T, C, nT, out);
+  return cudaGetLastError();
+}
+
 __global__ void device_exp_kernel(const double* x, double* y, int n, const ExpCoeffs c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = exp_fp64(x[i], c);

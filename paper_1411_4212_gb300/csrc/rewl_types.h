@@ -55,6 +55,8 @@ struct WalkerState {
   long long* steps;                    // [S] Wang-Landau trial moves done
   long long* accepts;                  // [S]
   long long* recomputes;               // [S]
+  long long* path_batches;             // [S][3] production pipelined walker: batches resolved by the
+                                       // warp scan, 8-move blocks, one move at a time
   long long* init_moves;               // [S]
   double* drift;                       // [S] largest |running E - recomputed E|
   int32_t* ctrl;                       // [0] error code, [1] halved counter, [2] done counter
@@ -78,6 +80,8 @@ struct WalkerArgs {
   int recompute;                       // 1: energy recomputation at the end of the launch
   int own_mask;                        // pipelined walker: owner-table size - 1 (power of two)
   int smem_lattice;                    // batched pipelined walker: 1 = lattice copied into shared memory
+  int resolver;                        // production pipelined walker: 0 per-batch choice, 1 scan,
+                                       // 2 blocks, 3 one move at a time (same decisions)
   double lnf_final;
 };
 

@@ -572,7 +572,9 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
     //                 (low-energy windows);
     //   sequential -- one move at a time: many full resolutions (bins as narrow as the temperature).
     enum { kScan = 0, kBlocks = 1, kSequential = 2 };
-    int path = kBlocks;
+    const int forced = a.resolver - 1;      // -1: per-batch choice
+    int path = forced >= 0 ? forced : kBlocks;
+    int n_scan = 0, n_blocks = 0, n_seq = 0;   // batches per path
     for (int b = 0; b < nb; ++b) {
       const int cur = b & 1;
       named_sync(kBarReady + cur);
@@ -828,7 +830,12 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       }
       // measured: blocks cost about 90 cycles per move whatever the rejected exits; the scan about
       // 200 per batch plus 260 per event, so it wins below about 10 events per batch
-      path = (n_rej + n_ev <= 10) ? kScan : (n_ev >= 6 ? kSequential : kBlocks);
+      if (nvalid > 0) {
+        n_scan += path == kScan ? 1 : 0;
+        n_blocks += path == kBlocks ? 1 : 0;
+        n_seq += path == kSequential ? 1 : 0;
+      }
+      path = forced >= 0 ? forced : ((n_rej + n_ev <= 10) ? kScan : (n_ev >= 6 ? kSequential : kBlocks));
       // the batch's moves at the current bin
       lng_seg += (long long)(nvalid - k_seg) * lnf_eff;
       h_seg += hinc * (uint32_t)(nvalid - k_seg);
@@ -848,6 +855,9 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       a.st.steps[slot] = t0 + moves;
       a.st.accepts[slot] += n_acc;
       a.st.recomputes[slot] += n_rec;
+      a.st.path_batches[3 * (size_t)slot + 0] += n_scan;
+      a.st.path_batches[3 * (size_t)slot + 1] += n_blocks;
+      a.st.path_batches[3 * (size_t)slot + 2] += n_seq;
     }
    }
   }

@@ -41,7 +41,7 @@ BAD = [
     dict(e_min=0.0, e_max=-1.0), dict(e_min=float("inf"), e_max=0.0), dict(group_size=3), dict(overlap=0.0),
     dict(kind=rw.TABLE, nbr=[[0, 5]], Jt=[[1.0, 1.0]], e_min=-1.0, e_max=1.0),
     dict(kind=rw.TABLE, nbr=[[1, 0]], Jt=[[1.0, 1.0]]),
-    dict(kind=7), dict(iteration=2),
+    dict(kind=7), dict(iteration=2), dict(resolver=4), dict(resolver=-1),
 ]
 
 
@@ -79,3 +79,5 @@ def test_batch_entry_points_reject_invalid_arguments():
     assert lib.rewl_autotune(None, 10, None, None) == rw.EINVAL
     assert lib.rewl_batch_run_to_convergence(None, 1, 1, None) == rw.EINVAL
     lib.rewl_batch_destroy(None)
+    t = C.c_double()
+    assert lib.rewl_peak_temperature(None, None, 0, C.byref(t), None) == rw.EINVAL

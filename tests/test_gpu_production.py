@@ -1,9 +1,10 @@
 """Production mode (FP32 spins and dE; ln g and energy in 64-bit fixed point) against exact results
 and, statistically, against the FP64 oracle; plus state invariants at the benchmark geometry and at
 the large 4-shell L=32 geometry (global-memory lattice path)."""
+import json
 import math
+import os
 import time
-from multiprocessing import get_context
 
 import numpy as np
 import pytest
@@ -48,55 +49,89 @@ def test_production_chain_matches_exact_density_of_states():
     assert np.max(np.abs(devs.mean(0))) < 0.12
 
 
-STAT_CFG = dict(L=4, J=(1.0, 0.5), e_min=-400.0, e_max=0.0, n_bins=120, n_windows=4, walkers_per_window=2,
-                overlap=0.75, flatness=0.8, lnf_final=1e-4, exchange_interval=10000)
-T_GRID = np.linspace(1.5, 4.0, 2501)
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "production_reference_bcc4.json")
 
 
-def _oracle_run(seed):
-    s = oracle.OracleREWL(kind=oracle.BCC, seed=seed, **STAT_CFG)
-    s.init_walkers()
-    while not s.all_done(STAT_CFG["lnf_final"]):
-        s.run_intervals(10)
-    lng, cen = s.merge()
-    U, Cv, _ = oracle.thermo(lng, cen, s.N, T_GRID)
-    return lng, oracle.peak(T_GRID, Cv)
+def _reference():
+    with open(GOLDEN) as f:
+        ref = json.load(f)
+    cfg = dict(ref["config"])
+    cfg["J"] = tuple(cfg["J"])
+    return ref, cfg, np.linspace(**ref["T_grid"])
+
+
+def _converge_concurrently(jobs, lnf_final, chunk=20, limit_s=900):
+    """Every job on its own CUDA stream: enqueue chunks of intervals for all unfinished jobs, then
+    check them (each check synchronises only that job's stream)."""
+    t0 = time.time()
+    left = list(jobs)
+    while left:
+        for g in left:
+            g.run_intervals(chunk, stats=False)
+        left = [g for g in left if not np.all(g.walkers()["lnf"] < lnf_final)]
+        assert time.time() - t0 < limit_s, "runs did not converge in time"
 
 
 @pytest.mark.parametrize("group_size", [0, 1])
 def test_production_statistics_match_oracle(group_size):
-    """16 seeds each side: normalised ln g and the specific-heat peak agree within the stated
-    tolerance (0.02 rms, 0.5 %) or, where the seed-to-seed noise of Wang-Landau itself is larger,
-    within three standard errors of the difference.  group_size 0 picks the batch walker (8 lanes
-    per move at N = 128); 1 forces the warp-specialised walker, whose 64-move speculation window
-    conflicts constantly on 128 spins."""
-    seeds = list(range(1, 17))
-    with get_context("spawn").Pool(min(16, len(seeds))) as pool:
-        ores = pool.map(_oracle_run, [1000 + s for s in seeds])
-    lo = np.array([r[0] for r in ores])
-    to = np.array([r[1] for r in ores])
+    """Production mode against the FP64 oracle at the stated tolerance: the normalised ln g over bins
+    within 0.02 rms, and the specific-heat peak temperature within 0.5 %.
+
+    A single seed of plain Wang-Landau has a saturated error here: the per-seed spread is 0.06-0.07 rms
+    at ln f_final = 1e-5, 1e-6 and 1e-7.  The 8-seed error bar (about 0.024 rms, 0.5 % in T) is
+    therefore as large as the tolerance itself.  So both sides average 256 seeds.  The oracle's are
+    stored in tests/golden/production_reference_bcc4.json, written by make_production_reference.py
+    beside it from oracle/ alone.  The test asserts the tolerance as stated.  It also asserts that the
+    noise of the comparison, reported beside it with the 8-seed error bars, is well below the tolerance.
+
+    group_size 0 picks the batch walker (8 lanes per move at N = 128; the runs go concurrently, one
+    stream each).  group_size 1 forces the warp-specialised walker, which takes most of its batches from
+    the one-move-at-a-time path at 128 spins (nearly every move of its 64 in flight is corrected).
+    Its 256 runs go in one batched launch."""
+    import torch
+    ref, cfg, T = _reference()
+    n = ref["n_seeds"]
+    lo_mean, lo_sd = np.array(ref["lng_mean"]), np.array(ref["lng_sd"])
+    to = np.array(ref["tpeak"])
+    seeds = [1 + i for i in range(n)]
+    streams = [torch.cuda.Stream() for _ in seeds] if group_size == 0 else [None] * n
+    jobs = [rw.REWL(kind=rw.BCC, seed=s, mode=rw.PRODUCTION, group_size=group_size, stream=st, **cfg)
+            for s, st in zip(seeds, streams)]
+    assert all(g.info()["pipelined"] == (1 if group_size == 1 else 0) for g in jobs)
+    t0 = time.time()
+    if group_size == 1:
+        with rw.Batch(jobs) as b:
+            ok, done = b.run_to_convergence(max_intervals=20000, check_every=16)
+            assert ok and done == n
+    else:
+        _converge_concurrently(jobs, cfg["lnf_final"])
+    torch.cuda.synchronize()
+    wall = time.time() - t0
     lg, tg = [], []
-    for s in seeds:
-        g = rw.REWL(kind=rw.BCC, seed=s, mode=rw.PRODUCTION, group_size=group_size, **STAT_CFG)
-        assert g.info()["pipelined"] == (1 if group_size == 1 else 0)
-        run_to_end(g, STAT_CFG["lnf_final"])
+    for g in jobs:
+        assert np.all(g.walkers()["lnf"] < cfg["lnf_final"])
         lng, cen = g.merge()
-        U, Cv, _ = rw.thermo(lng, cen, g.N, T_GRID)
+        _, Cv, _ = rw.thermo(lng, cen, g.N, T)
         lg.append(lng)
-        tg.append(rw.peak_temperature(T_GRID, Cv))
+        tg.append(rw.peak_temperature(T, Cv))
         g.close()
     lg, tg = np.array(lg), np.array(tg)
-    n = len(seeds)
-    diff = lg.mean(0) - lo.mean(0)
+    diff = lg.mean(0) - lo_mean
     rms = float(np.sqrt(np.mean(diff ** 2)))
-    noise = float(np.sqrt(np.mean(lg.var(0, ddof=1) / n + lo.var(0, ddof=1) / n)))
+    noise = float(np.sqrt(np.mean(lg.var(0, ddof=1) / n + lo_sd ** 2 / n)))
     dT = float(tg.mean() - to.mean())
+    rel_T = abs(dT) / to.mean()
     sT = float(math.sqrt(tg.var(ddof=1) / n + to.var(ddof=1) / n))
-    print(f"ln g rms(mean GPU - mean oracle) = {rms:.4f} (noise {noise:.4f}); "
-          f"T_peak GPU {tg.mean():.4f} +- {tg.std(ddof=1) / math.sqrt(n):.4f}, "
-          f"oracle {to.mean():.4f} +- {to.std(ddof=1) / math.sqrt(n):.4f}")
-    assert rms <= max(0.02, 3.0 * noise)
-    assert abs(dT) <= max(0.005 * to.mean(), 3.0 * sT)
+    eb8 = float(np.sqrt(np.mean(lg.var(0, ddof=1) / 8)))
+    print(f"{n} seeds each side ({wall:.1f} s on the GPU): ln g rms(mean GPU - mean oracle) = {rms:.4f} "
+          f"(noise of the comparison {noise:.4f}; 8-seed error bar {eb8:.4f}); "
+          f"T_peak GPU {tg.mean():.4f} +- {tg.std(ddof=1) / math.sqrt(n):.4f} "
+          f"(8-seed error bar {tg.std(ddof=1) / math.sqrt(8):.4f}), oracle {to.mean():.4f} +- "
+          f"{to.std(ddof=1) / math.sqrt(n):.4f}: {100 * rel_T:.2f} %")
+    # the comparison resolves the stated tolerance
+    assert 3.0 * noise < 0.02 and 3.0 * sT < 0.005 * to.mean()
+    assert rms <= 0.02
+    assert rel_T <= 0.005
 
 
 def test_benchmark_geometry_invariants():
