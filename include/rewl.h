@@ -310,6 +310,81 @@ const char* rewl_last_error(const rewl_handle* h);
 /* Release everything; NULL-safe. */
 void rewl_destroy(rewl_handle* h);
 
+/* ---- Partitioned runs: one REWL run split over several handles (one per GPU) -------------------
+ * The paper runs every walker as its own process and exchanges replicas between processes of
+ * adjacent windows (Sec. 4.3, Eq. 5).  Here a run of h windows x m walkers can be split over handles
+ * by contiguous window ranges, one handle per GPU.  The window ranges are those at creation.
+ * A handle hosts S = (window_end - window_begin) m positions.  Each position holds one
+ * configuration (lattice and energy) for the whole run, and one slot state: the ln g and H of a
+ * window, ln f, the stage, and the Philox key and counter of a global slot s = k m + a.  Exchanges
+ * between two slots of one handle swap their configurations by index, as rewl_exchange does.  An
+ * accepted exchange between slots of different handles moves the two slot states between the
+ * handles (a few KB) and leaves the configurations where they are, so a handle comes to host slots
+ * of other windows.  The run is the same Markov chain as the single handle, slot for slot: in
+ * trajectory mode bit for bit.  A round of replica exchange is driven by the caller, who combines
+ * per-slot arrays over the handles (elementwise max of rewl_partition_bins, sum of
+ * rewl_partition_lookups: every entry is written by exactly one handle):
+ *   1. bins_all  = combine(rewl_partition_bins of every handle)        (-1 before: max)
+ *   2. lk_all    = combine(rewl_partition_lookups(bins_all) of every handle)   (0 before: sum)
+ *   3. rewl_partition_exchange(bins_all, lk_all) on every handle -> swap_with
+ *   4. for every hosted slot g with swap_with[g] = o >= 0: export g, import the state of o (exported by
+ *      the handle hosting o) in its place (rewl_slot_export, rewl_slot_import)
+ *   5. rewl_partition_observe on every handle (round trips).
+ * Wang-Landau moves (rewl_walk) and the flatness test (rewl_flatness) run per handle.  Not available
+ * on a partitioned handle: rewl_run_intervals, rewl_run_stage, rewl_exchange, the merge (gather the
+ * fragments by global slot and call rewl_stitch_device), batches, REWL_ITERATION_WINDOW. */
+
+/* Create the handle of windows [window_begin, window_end) of the run that rewl_create would create
+ * with the same arguments (every handle of the run passes the same arguments but its own range).
+ * REWL_EINVAL also when the range is empty or outside [0, n_windows). */
+rewl_status rewl_create_partition(const rewl_lattice* lattice, const rewl_couplings* couplings,
+                                  const rewl_windows* windows, int walkers_per_window, double overlap,
+                                  double flatness, double lnf_final, const rewl_config* config,
+                                  int window_begin, int window_end, rewl_handle** out);
+
+/* Global slot hosted at each position: gid host [n_slots of rewl_get_info] (0..S-1 for a plain handle). */
+rewl_status rewl_partition_slots(rewl_handle* h, int32_t* gid);
+
+/* Step 1 of a round: bins host [h m]; the bin of the configuration at each position is written at
+ * the global slot the position hosts; the other entries are left as they are.  Blocks. */
+rewl_status rewl_partition_bins(rewl_handle* h, int32_t* bins);
+
+/* Step 2: with bins_all (host [h m], every slot's bin), for every pair of the coming round with
+ * exactly one slot here, that slot's ln g at its own configuration's bin and at the partner's:
+ * lk host [2 h m], entries 2g and 2g+1 of each hosted slot g (0 where the slot is in no such pair or
+ * the partner's bin lies outside its window).  The values are the 64 bits of the ln g tables:
+ * 2^-40 fixed point (production) or the FP64 bit pattern (trajectory).  Other entries are left
+ * as they are.  Blocks. */
+rewl_status rewl_partition_lookups(rewl_handle* h, const int32_t* bins_all, int64_t* lk);
+
+/* Step 3, the round (Sec. 4.3, Eq. 5; pairing as rewl_exchange): pairs with both slots here swap
+ * their configurations; pairs with one slot here are decided from bins_all and lk_all (host [h m],
+ * [2 h m], combined over the handles), D = ((ln g_i(E_A) - ln g_i(E_B)) + ln g_j(E_B)) - ln g_j(E_A)
+ * in FP64 and the same Philox uniform, so both handles of a pair take the same decision.  swap_with
+ * host [h m]: for each hosted slot in an accepted cross-handle pair the partner's global slot,
+ * -1 elsewhere.  The handle hosting the pair's lower slot counts the attempt and the acceptance
+ * (rewl_get_exchange_counts: sum over the handles).  Blocks. */
+rewl_status rewl_partition_exchange(rewl_handle* h, const int32_t* bins_all, const int64_t* lk_all,
+                                    int32_t* swap_with);
+
+/* Step 5: after the slot states have moved, the configurations of the extreme windows are looked at
+ * again (Sec. 5 round trips, counted per configuration of the handle).  Stream-ordered. */
+rewl_status rewl_partition_observe(rewl_handle* h);
+
+/* Size in bytes of a slot state buffer (rewl_slot_export / rewl_slot_import). */
+rewl_status rewl_slot_state_bytes(rewl_handle* h, int64_t* bytes);
+
+/* Copy the state of hosted global slot g into buf (host, rewl_slot_state_bytes): ln g and H of its
+ * window, ln f, stage, trial moves done (the Philox counter), accept and correction counters, moves
+ * of the initial drive, largest energy drift, resolver-path batch counts, and g itself.  Blocks. */
+rewl_status rewl_slot_export(rewl_handle* h, int32_t g, void* buf);
+
+/* Replace hosted slot g_out by the slot state in buf (exported by a handle of the same run): the
+ * position keeps its configuration and from then on walks as the slot in buf (its window, Philox
+ * key and counter).  REWL_EINVAL if g_out is not hosted here, the buffer is not a slot state of a run
+ * with this window size and mode, or its slot is already hosted here.  Blocks. */
+rewl_status rewl_slot_import(rewl_handle* h, int32_t g_out, const void* buf);
+
 /* ---- Batches: many independent REWL jobs in one persistent walker launch ----------------------
  * A batch runs the exchange intervals (Sec. 4.2-4.3: Wang-Landau moves, replica exchange,
  * flatness check and ln f reduction) of many handles at once.  All walker slots of all jobs form

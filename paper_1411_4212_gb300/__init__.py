@@ -141,6 +141,16 @@ def load_library(path=LIB_PATH):
         "rewl_thermo": ([_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, _vp, _vp, _vp], st),
         "rewl_set_initial_lng": ([_vp, _vp, C.c_double], st),
         "rewl_peak_temperature": ([_vp, _vp, C.c_int, C.POINTER(C.c_double), _vp], st),
+        "rewl_create_partition": ([C.POINTER(Lattice), C.POINTER(Couplings), C.POINTER(Windows), C.c_int, C.c_double,
+                                   C.c_double, C.c_double, C.POINTER(Config), C.c_int, C.c_int, C.POINTER(_vp)], st),
+        "rewl_partition_slots": ([_vp, _vp], st),
+        "rewl_partition_bins": ([_vp, _vp], st),
+        "rewl_partition_lookups": ([_vp, _vp, _vp], st),
+        "rewl_partition_exchange": ([_vp, _vp, _vp, _vp], st),
+        "rewl_partition_observe": ([_vp], st),
+        "rewl_slot_state_bytes": ([_vp, C.POINTER(C.c_int64)], st),
+        "rewl_slot_export": ([_vp, C.c_int32, _vp], st),
+        "rewl_slot_import": ([_vp, C.c_int32, _vp], st),
         "rewl_get_info": ([_vp, C.POINTER(Info)], st),
         "rewl_get_walkers": ([_vp] + [_vp] * 10, st),
         "rewl_get_spins": ([_vp, _vp], st),
@@ -213,7 +223,7 @@ class REWL:
                  n_bins=200, n_windows=4, walkers_per_window=2, overlap=0.75, flatness=0.8,
                  lnf_final=1e-3, seed=1, mode=PRODUCTION, group_size=0, exchange_interval=10000,
                  max_moves_per_stage=0, init_max_moves=0, recompute_every=0, lnf_initial=0.0,
-                 timeout_s=0.0, stream=None, iteration=0, resolver=RESOLVER_AUTO):
+                 timeout_s=0.0, stream=None, iteration=0, resolver=RESOLVER_AUTO, partition=None):
         lib = load_library()
         lat = Lattice()
         lat.kind = kind
@@ -247,8 +257,16 @@ class REWL:
         cfg.cuda_stream = _stream_ptr(stream)
         cfg.resolver = resolver
         h = _vp()
-        _check(lib.rewl_create(C.byref(lat), C.byref(cp), C.byref(win), walkers_per_window, overlap, flatness,
-                               lnf_final, C.byref(cfg), C.byref(h)))
+        if partition is None:
+            _check(lib.rewl_create(C.byref(lat), C.byref(cp), C.byref(win), walkers_per_window, overlap, flatness,
+                                   lnf_final, C.byref(cfg), C.byref(h)))
+            self.window_begin = 0
+        else:
+            k0, k1 = partition
+            _check(lib.rewl_create_partition(C.byref(lat), C.byref(cp), C.byref(win), walkers_per_window, overlap,
+                                             flatness, lnf_final, C.byref(cfg), int(k0), int(k1), C.byref(h)))
+            self.window_begin = int(k0)
+        self.partition = partition
         self._h = h
         self._lib = lib
         info = self.info()
@@ -399,6 +417,53 @@ class REWL:
 
     def centres(self):
         return self.e_min + (np.arange(self.B) + 0.5) * self.dE
+
+    # -- partitioned runs (see partition.py for the round protocol) -------------------------
+    @property
+    def n_global_slots(self):
+        return self.h * self.m
+
+    def partition_slots(self):
+        g = np.zeros(self.n_slots, dtype=np.int32)
+        _check(self._lib.rewl_partition_slots(self._h, _ptr(g)), self._h)
+        return g
+
+    def partition_bins(self, bins):
+        """Write the bins of the hosted slots' configurations into bins (int32 [h m]) in place."""
+        assert bins.dtype == np.int32 and bins.flags.c_contiguous and bins.size == self.n_global_slots
+        _check(self._lib.rewl_partition_bins(self._h, _ptr(bins)), self._h)
+
+    def partition_lookups(self, bins_all, lk):
+        """Write the hosted slots' ln g lookups of the coming round into lk (int64 [2 h m]) in place."""
+        bins_all = np.ascontiguousarray(bins_all, dtype=np.int32)
+        assert lk.dtype == np.int64 and lk.flags.c_contiguous and lk.size == 2 * self.n_global_slots
+        _check(self._lib.rewl_partition_lookups(self._h, _ptr(bins_all), _ptr(lk)), self._h)
+
+    def partition_exchange(self, bins_all, lk_all):
+        """The exchange round; returns swap_with (int32 [h m])."""
+        bins_all = np.ascontiguousarray(bins_all, dtype=np.int32)
+        lk_all = np.ascontiguousarray(lk_all, dtype=np.int64)
+        sw = np.zeros(self.n_global_slots, dtype=np.int32)
+        _check(self._lib.rewl_partition_exchange(self._h, _ptr(bins_all), _ptr(lk_all), _ptr(sw)), self._h)
+        return sw
+
+    def partition_observe(self):
+        _check(self._lib.rewl_partition_observe(self._h), self._h)
+
+    def slot_state_words(self):
+        n = C.c_int64()
+        _check(self._lib.rewl_slot_state_bytes(self._h, C.byref(n)), self._h)
+        return n.value // 8
+
+    def slot_export(self, g):
+        buf = np.zeros(self.slot_state_words(), dtype=np.int64)
+        _check(self._lib.rewl_slot_export(self._h, int(g), _ptr(buf)), self._h)
+        return buf
+
+    def slot_import(self, g_out, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.int64)
+        assert buf.size == self.slot_state_words()
+        _check(self._lib.rewl_slot_import(self._h, int(g_out), _ptr(buf)), self._h)
 
 
 class Batch:

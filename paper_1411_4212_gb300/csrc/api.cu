@@ -49,6 +49,17 @@ struct rewl_handle {
   bool pipe_smem_lattice = false;
   size_t pipe_smem_bytes = 0;
   int own_entries = 0;
+  // partitioned handle (rewl_create_partition): hosts windows [k_begin, k_end) of an h-window run at
+  // creation; slot states move between the run's handles on accepted cross-handle exchanges
+  bool part = false;
+  int k_begin = 0, k_end = 0, S_global = 0;
+  std::vector<int32_t> gid_host;   // [S] global slot hosted at each position
+  std::vector<int32_t> pos_host;   // [S_global] position of each hosted global slot, -1 elsewhere
+  int32_t* d_gid = nullptr;
+  int32_t* d_pos_of = nullptr;
+  int32_t* d_part_bins = nullptr;  // [S_global]
+  long long* d_part_lk = nullptr;  // [2 S_global]
+  int32_t* d_part_swap = nullptr;  // [S_global]
 
   void* d_spins = nullptr;
   int32_t* d_perm = nullptr;
@@ -204,6 +215,9 @@ WalkerState state_of(rewl_handle* h) {
   s.rt_count = h->d_rt_count;
   s.ex_att = h->d_ex_att;
   s.ex_acc = h->d_ex_acc;
+  s.gid = h->d_gid;
+  s.pos_of = h->d_pos_of;
+  s.S_global = h->S_global;
   return s;
 }
 
@@ -278,6 +292,19 @@ rewl_status check_ready(rewl_handle* h) {
   return REWL_OK;
 }
 
+int global_of(const rewl_handle* h, int p) { return h->part ? h->gid_host[p] : p; }
+
+// Calls that need every slot of the run in one handle.
+rewl_status check_whole(rewl_handle* h) {
+  rewl_status s = check_ready(h);
+  if (s != REWL_OK) return s;
+  if (h->part)
+    return fail(h, REWL_ESTATE,
+                "partitioned handle: the replica exchange goes through rewl_partition_exchange and the merge "
+                "through rewl_stitch_device on the gathered fragments");
+  return REWL_OK;
+}
+
 }  // namespace
 
 void rewl::set_handleless_error(const std::string& msg) { g_last_error = msg; }
@@ -296,9 +323,11 @@ void rewl_destroy(rewl_handle* h) {
   delete h;
 }
 
-rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, const rewl_windows* win,
-                        int walkers_per_window, double overlap, double flatness, double lnf_final,
-                        const rewl_config* cfg, rewl_handle** out) {
+}  // extern "C"
+
+static rewl_status create_impl(const rewl_lattice* lat, const rewl_couplings* cpl, const rewl_windows* win,
+                               int walkers_per_window, double overlap, double flatness, double lnf_final,
+                               const rewl_config* cfg, bool part, int k_begin, int k_end, rewl_handle** out) {
   if (!out) return fail(nullptr, REWL_EINVAL, "out is NULL");
   *out = nullptr;
   if (!lat || !cpl || !win || !cfg) return fail(nullptr, REWL_EINVAL, "NULL argument");
@@ -470,7 +499,22 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   if (h->W < 2) return bad("windows narrower than 2 bins");
   for (int k = 0; k + 1 < h->h; ++k)
     if (h->starts[k] + h->W - h->starts[k + 1] < 2) return bad("adjacent windows overlap by fewer than 2 bins");
-  h->S = h->h * h->m;
+  h->S_global = h->h * h->m;
+  h->S = h->S_global;
+  if (part) {
+    if (k_begin < 0 || k_end > h->h || k_begin >= k_end) return bad("partition windows must satisfy 0 <= window_begin < window_end <= n_windows");
+    if (h->by_window) return bad("a partitioned run needs REWL_ITERATION_WALKER (a window's walkers may sit in different handles)");
+    h->part = true;
+    h->k_begin = k_begin;
+    h->k_end = k_end;
+    h->S = (k_end - k_begin) * h->m;
+    h->gid_host.resize(h->S);
+    h->pos_host.assign(h->S_global, -1);
+    for (int p2 = 0; p2 < h->S; ++p2) {
+      h->gid_host[p2] = k_begin * h->m + p2;
+      h->pos_host[k_begin * h->m + p2] = p2;
+    }
+  }
 
   // ---- lanes per move ----
   if (cfg->group_size == 0) {
@@ -571,6 +615,13 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   A(&h->d_avg, (size_t)h->h * W);
   A(&h->d_bstar, std::max(h->h - 1, 1));
   A(&h->d_merge, h->B);
+  if (h->part) {
+    A(&h->d_gid, S);
+    A(&h->d_pos_of, h->S_global);
+    A(&h->d_part_bins, h->S_global);
+    A(&h->d_part_lk, 2 * (size_t)h->S_global);
+    A(&h->d_part_swap, h->S_global);
+  }
   if (g.kind == 1) {
     A(&h->d_tab_nbr, (size_t)h->z * N);
     A(&h->d_tab_Jf, (size_t)h->z * N);
@@ -641,6 +692,10 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   zero(h->d_ex_att, std::max(h->h - 1, 1) * sizeof(unsigned long long));
   zero(h->d_ex_acc, std::max(h->h - 1, 1) * sizeof(unsigned long long));
   up(h->d_starts, h->starts.data(), h->h * sizeof(int32_t));
+  if (h->part) {
+    up(h->d_gid, h->gid_host.data(), S * sizeof(int32_t));
+    up(h->d_pos_of, h->pos_host.data(), h->S_global * sizeof(int32_t));
+  }
   if (g.kind == 1) {
     std::vector<float> jf(h->tab_J.size());
     for (size_t t = 0; t < jf.size(); ++t) jf[t] = (float)h->tab_J[t];
@@ -656,6 +711,21 @@ rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, cons
   }
   *out = h;
   return REWL_OK;
+}
+
+extern "C" {
+
+rewl_status rewl_create(const rewl_lattice* lat, const rewl_couplings* cpl, const rewl_windows* win,
+                        int walkers_per_window, double overlap, double flatness, double lnf_final,
+                        const rewl_config* cfg, rewl_handle** out) {
+  return create_impl(lat, cpl, win, walkers_per_window, overlap, flatness, lnf_final, cfg, false, 0, 0, out);
+}
+
+rewl_status rewl_create_partition(const rewl_lattice* lat, const rewl_couplings* cpl, const rewl_windows* win,
+                                  int walkers_per_window, double overlap, double flatness, double lnf_final,
+                                  const rewl_config* cfg, int window_begin, int window_end, rewl_handle** out) {
+  return create_impl(lat, cpl, win, walkers_per_window, overlap, flatness, lnf_final, cfg, true, window_begin,
+                     window_end, out);
 }
 
 rewl_status rewl_init_walkers(rewl_handle* h) {
@@ -706,6 +776,7 @@ void rewl::job_view(const rewl_handle* h, JobView* v) {
   v->exchange_interval = h->exchange_interval;
   v->recompute_every = h->recompute_every;
   v->stream = h->stream;
+  v->part = h->part;
 }
 
 WalkerArgs rewl::job_walker_args(rewl_handle* h, long long moves, int recompute) {
@@ -898,7 +969,7 @@ static rewl_status read_stage(rewl_handle* h, std::vector<int32_t>& stage, std::
 }
 
 rewl_status rewl_run_intervals(rewl_handle* h, int n, rewl_stage_stats* stats) {
-  rewl_status s = check_ready(h);
+  rewl_status s = check_whole(h);
   if (s != REWL_OK) return s;
   if (n < 0) return fail(h, REWL_EINVAL, "n_intervals must be >= 0");
   if (!h->initialized) {
@@ -926,7 +997,7 @@ rewl_status rewl_run_intervals(rewl_handle* h, int n, rewl_stage_stats* stats) {
 }
 
 rewl_status rewl_run_stage(rewl_handle* h, rewl_stage_stats* stats) {
-  rewl_status s = check_ready(h);
+  rewl_status s = check_whole(h);
   if (s != REWL_OK) return s;
   if (!h->initialized) {
     s = rewl_init_walkers(h);
@@ -971,7 +1042,7 @@ rewl_status rewl_run_stage(rewl_handle* h, rewl_stage_stats* stats) {
 }
 
 rewl_status rewl_exchange(rewl_handle* h, rewl_stage_stats* stats) {
-  rewl_status s = check_ready(h);
+  rewl_status s = check_whole(h);
   if (s != REWL_OK) return s;
   if (!h->initialized) {
     s = rewl_init_walkers(h);
@@ -1004,7 +1075,7 @@ static MergeArgs merge_args(rewl_handle* h, double* out) {
 }
 
 rewl_status rewl_merge_lng_device(rewl_handle* h, double* out) {
-  rewl_status s = check_ready(h);
+  rewl_status s = check_whole(h);
   if (s != REWL_OK) return s;
   if (!out) return fail(h, REWL_EINVAL, "lng_out_dev is NULL");
   CUDA_TRY(h, launch_merge(merge_args(h, out), h->stream));
@@ -1012,7 +1083,7 @@ rewl_status rewl_merge_lng_device(rewl_handle* h, double* out) {
 }
 
 rewl_status rewl_merge_lng(rewl_handle* h, double* lng_out, double* centres) {
-  rewl_status s = check_ready(h);
+  rewl_status s = check_whole(h);
   if (s != REWL_OK) return s;
   if (!lng_out) return fail(h, REWL_EINVAL, "lng_out is NULL");
   CUDA_TRY(h, launch_merge(merge_args(h, h->d_merge), h->stream));
@@ -1115,13 +1186,13 @@ rewl_status rewl_set_initial_lng(rewl_handle* h, const double* lng, double lnf0)
   if (h->traj) {
     std::vector<double> t(S * W);
     for (size_t s2 = 0; s2 < S; ++s2)
-      for (size_t w = 0; w < W; ++w) t[s2 * W + w] = lng[h->starts[s2 / h->m] + w];
+      for (size_t w = 0; w < W; ++w) t[s2 * W + w] = lng[h->starts[global_of(h, (int)s2) / h->m] + w];
     CUDA_TRY(h, cudaMemcpyAsync(h->d_lng, t.data(), S * W * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   } else {
     std::vector<long long> t(S * W);
     for (size_t s2 = 0; s2 < S; ++s2)
-      for (size_t w = 0; w < W; ++w) t[s2 * W + w] = std::llrint(lng[h->starts[s2 / h->m] + w] * kLngScale);
+      for (size_t w = 0; w < W; ++w) t[s2 * W + w] = std::llrint(lng[h->starts[global_of(h, (int)s2) / h->m] + w] * kLngScale);
     std::vector<long long> lf(S, std::llrint(lnf0 * kLngScale));
     for (auto& v : lnf) v = (double)lf[0] * kLngUnit;
     CUDA_TRY(h, cudaMemcpyAsync(h->d_lng_fx, t.data(), S * W * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
@@ -1304,6 +1375,199 @@ rewl_status rewl_replica_energies(rewl_handle* h, double* E) {
   CUDA_TRY(h, cudaMemcpyAsync(E, d, h->S * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaFreeAsync(d, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return REWL_OK;
+}
+
+// ---- partitioned runs ----------------------------------------------------------------------------
+// Slot state (rewl_slot_export): int64 words
+//   [0] tag, [1] global slot, [2] W, [3] mode, [4] ln f (FP64 bits), [5] ln f (2^-40 fixed point),
+//   [6] stage, [7] trial moves done (the Philox counter), [8] accepts, [9] corrections, [10] moves of
+//   the initial drive, [11] largest energy drift (FP64 bits), [12..14] batches per resolver path,
+//   [15 .. 15+W) ln g (fixed point or FP64 bits), then H packed two u32 per word.
+constexpr long long kSlotTag = 0x5245574c534c4f54LL;   // "REWLSLOT"
+constexpr int kSlotHead = 15;
+
+static int64_t slot_words(const rewl_handle* h) { return kSlotHead + h->W + (h->W + 1) / 2; }
+
+static ExchangeArgs exchange_args(rewl_handle* h) {
+  ExchangeArgs ea{};
+  ea.win = windows_of(h);
+  ea.st = state_of(h);
+  ea.ex = h->ex;
+  ea.key1 = h->key1;
+  ea.traj = h->traj ? 1 : 0;
+  if (h->part) {
+    ea.part_bin_all = h->d_part_bins;
+    ea.part_lk_all = h->d_part_lk;
+    ea.part_swap_with = h->d_part_swap;
+  }
+  return ea;
+}
+
+static rewl_status check_part(rewl_handle* h) {
+  rewl_status s = check_ready(h);
+  if (s != REWL_OK) return s;
+  if (!h->part) return fail(h, REWL_ESTATE, "not a partitioned handle (rewl_create_partition)");
+  if (!h->initialized) return fail(h, REWL_ESTATE, "walkers not initialised (rewl_init_walkers)");
+  return REWL_OK;
+}
+
+rewl_status rewl_partition_slots(rewl_handle* h, int32_t* gid) {
+  rewl_status s = check_ready(h);
+  if (s != REWL_OK) return s;
+  if (!gid) return fail(h, REWL_EINVAL, "gid is NULL");
+  for (int p2 = 0; p2 < h->S; ++p2) gid[p2] = global_of(h, p2);
+  return REWL_OK;
+}
+
+rewl_status rewl_partition_bins(rewl_handle* h, int32_t* bins) {
+  rewl_status s = check_part(h);
+  if (s != REWL_OK) return s;
+  if (!bins) return fail(h, REWL_EINVAL, "bins is NULL");
+  std::vector<int32_t> t(h->S_global);
+  CUDA_TRY(h, launch_partition_bins(exchange_args(h), h->S, h->d_part_bins, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(t.data(), h->d_part_bins, h->S_global * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  for (int p2 = 0; p2 < h->S; ++p2) bins[h->gid_host[p2]] = t[h->gid_host[p2]];
+  return REWL_OK;
+}
+
+rewl_status rewl_partition_lookups(rewl_handle* h, const int32_t* bins_all, int64_t* lk) {
+  rewl_status s = check_part(h);
+  if (s != REWL_OK) return s;
+  if (!bins_all || !lk) return fail(h, REWL_EINVAL, "NULL argument");
+  std::vector<long long> t(2 * (size_t)h->S_global);
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_part_bins, bins_all, h->S_global * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_part_lk, 0, t.size() * sizeof(long long), h->stream));
+  CUDA_TRY(h, launch_partition_lookups(exchange_args(h), h->d_part_bins, h->d_part_lk, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(t.data(), h->d_part_lk, t.size() * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  for (int p2 = 0; p2 < h->S; ++p2) {
+    const int g = h->gid_host[p2];
+    lk[2 * g] = t[2 * (size_t)g];
+    lk[2 * g + 1] = t[2 * (size_t)g + 1];
+  }
+  return REWL_OK;
+}
+
+rewl_status rewl_partition_exchange(rewl_handle* h, const int32_t* bins_all, const int64_t* lk_all, int32_t* swap_with) {
+  rewl_status s = check_part(h);
+  if (s != REWL_OK) return s;
+  if (!bins_all || !lk_all || !swap_with) return fail(h, REWL_EINVAL, "NULL argument");
+  const size_t S = h->S_global;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_part_bins, bins_all, S * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_part_lk, lk_all, 2 * S * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_part_swap, 0xff, S * sizeof(int32_t), h->stream));
+  CUDA_TRY(h, launch_exchange(exchange_args(h), h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(swap_with, h->d_part_swap, S * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return REWL_OK;
+}
+
+rewl_status rewl_partition_observe(rewl_handle* h) {
+  rewl_status s = check_part(h);
+  if (s != REWL_OK) return s;
+  CUDA_TRY(h, launch_partition_observe(exchange_args(h), h->stream));
+  return REWL_OK;
+}
+
+rewl_status rewl_slot_state_bytes(rewl_handle* h, int64_t* bytes) {
+  rewl_status s = check_ready(h);
+  if (s != REWL_OK) return s;
+  if (!bytes) return fail(h, REWL_EINVAL, "bytes is NULL");
+  *bytes = slot_words(h) * 8;
+  return REWL_OK;
+}
+
+rewl_status rewl_slot_export(rewl_handle* h, int32_t g, void* buf) {
+  rewl_status s = check_part(h);
+  if (s != REWL_OK) return s;
+  if (!buf || g < 0 || g >= h->S_global || h->pos_host[g] < 0) return fail(h, REWL_EINVAL, "slot not hosted here or NULL buffer");
+  const int p2 = h->pos_host[g];
+  const size_t W = h->W;
+  std::vector<long long> w(slot_words(h), 0);
+  std::vector<uint32_t> H(W);
+  double lnf = 0, drift = 0;
+  long long lnf_fx = 0, steps = 0, acc = 0, rec = 0, init = 0, pb[3] = {0, 0, 0};
+  int32_t stage = 0;
+  cudaStream_t st = h->stream;
+  CUDA_TRY(h, cudaMemcpyAsync(&lnf, h->d_lnf + p2, 8, cudaMemcpyDeviceToHost, st));
+  if (!h->traj) CUDA_TRY(h, cudaMemcpyAsync(&lnf_fx, h->d_lnf_fx + p2, 8, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(&stage, h->d_stage + p2, 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(&steps, h->d_steps + p2, 8, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(&acc, h->d_accepts + p2, 8, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(&rec, h->d_recomputes + p2, 8, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(&init, h->d_init_moves + p2, 8, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(&drift, h->d_drift + p2, 8, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(pb, h->d_path_batches + 3 * (size_t)p2, 24, cudaMemcpyDeviceToHost, st));
+  if (h->traj)
+    CUDA_TRY(h, cudaMemcpyAsync(w.data() + kSlotHead, h->d_lng + (size_t)p2 * W, W * 8, cudaMemcpyDeviceToHost, st));
+  else
+    CUDA_TRY(h, cudaMemcpyAsync(w.data() + kSlotHead, h->d_lng_fx + (size_t)p2 * W, W * 8, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaMemcpyAsync(H.data(), h->d_H + (size_t)p2 * W, W * 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaStreamSynchronize(st));
+  w[0] = kSlotTag;
+  w[1] = g;
+  w[2] = (long long)W;
+  w[3] = h->traj ? 1 : 0;
+  std::memcpy(&w[4], &lnf, 8);
+  w[5] = lnf_fx;
+  w[6] = stage;
+  w[7] = steps;
+  w[8] = acc;
+  w[9] = rec;
+  w[10] = init;
+  std::memcpy(&w[11], &drift, 8);
+  w[12] = pb[0];
+  w[13] = pb[1];
+  w[14] = pb[2];
+  std::memcpy(w.data() + kSlotHead + W, H.data(), W * 4);
+  std::memcpy(buf, w.data(), w.size() * 8);
+  return REWL_OK;
+}
+
+rewl_status rewl_slot_import(rewl_handle* h, int32_t g_out, const void* buf) {
+  rewl_status s = check_part(h);
+  if (s != REWL_OK) return s;
+  if (!buf || g_out < 0 || g_out >= h->S_global || h->pos_host[g_out] < 0)
+    return fail(h, REWL_EINVAL, "slot not hosted here or NULL buffer");
+  const size_t W = h->W;
+  std::vector<long long> w(slot_words(h));
+  std::memcpy(w.data(), buf, w.size() * 8);
+  const long long g_in = w[1];
+  if (w[0] != kSlotTag || w[2] != (long long)W || w[3] != (h->traj ? 1 : 0))
+    return fail(h, REWL_EINVAL, "buffer is not a slot state of this run (tag, window size or mode differ)");
+  if (g_in < 0 || g_in >= h->S_global || (g_in != g_out && h->pos_host[g_in] >= 0))
+    return fail(h, REWL_EINVAL, "incoming slot is out of range or already hosted here");
+  const int p2 = h->pos_host[g_out];
+  double lnf, drift;
+  std::memcpy(&lnf, &w[4], 8);
+  std::memcpy(&drift, &w[11], 8);
+  const int32_t stage = (int32_t)w[6], gi = (int32_t)g_in, none = -1;
+  cudaStream_t st = h->stream;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_lnf + p2, &lnf, 8, cudaMemcpyHostToDevice, st));
+  if (!h->traj) CUDA_TRY(h, cudaMemcpyAsync(h->d_lnf_fx + p2, &w[5], 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_stage + p2, &stage, 4, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_steps + p2, &w[7], 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_accepts + p2, &w[8], 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_recomputes + p2, &w[9], 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_init_moves + p2, &w[10], 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_drift + p2, &drift, 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_path_batches + 3 * (size_t)p2, &w[12], 24, cudaMemcpyHostToDevice, st));
+  if (h->traj)
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_lng + (size_t)p2 * W, w.data() + kSlotHead, W * 8, cudaMemcpyHostToDevice, st));
+  else
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_lng_fx + (size_t)p2 * W, w.data() + kSlotHead, W * 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_H + (size_t)p2 * W, w.data() + kSlotHead + W, W * 4, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_gid + p2, &gi, 4, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_pos_of + g_out, &none, 4, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_pos_of + gi, &p2, 4, cudaMemcpyHostToDevice, st));
+  // the pageable sources above are stack and vector memory: wait before they go out of scope
+  CUDA_TRY(h, cudaStreamSynchronize(st));
+  h->pos_host[g_out] = -1;
+  h->pos_host[gi] = p2;
+  h->gid_host[p2] = gi;
+  h->wargs_valid = false;
   return REWL_OK;
 }
 

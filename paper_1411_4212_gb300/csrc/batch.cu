@@ -287,6 +287,7 @@ extern "C" rewl_status rewl_batch_create(rewl_handle* const* jobs, int n_jobs, v
     if (v.broken) return bad(REWL_ESTATE, "job " + std::to_string(j) + " saw a CUDA error");
     if (v.kind != REWL_LATTICE_BCC || !v.pipe)
       return bad(REWL_EINVAL, "job " + std::to_string(j) + " does not use the pipelined bcc walker");
+    if (v.part) return bad(REWL_EINVAL, "job " + std::to_string(j) + " is a partitioned handle");
     if (v.traj != b->view[0].traj || v.n_shells != b->view[0].n_shells ||
         v.exchange_interval != b->view[0].exchange_interval || v.recompute_every != b->view[0].recompute_every)
       return bad(REWL_EINVAL, "jobs differ in mode, shell count, exchange_interval or recompute_every");

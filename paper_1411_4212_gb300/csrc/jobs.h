@@ -10,7 +10,7 @@ namespace rewl {
 
 struct JobView {
   int kind, N, z, L, S, W, h, m, n_shells;
-  bool traj, pipe, initialized, broken;
+  bool traj, pipe, initialized, broken, part;
   long long exchange_interval;
   int recompute_every;
   cudaStream_t stream;

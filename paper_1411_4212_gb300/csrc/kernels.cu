@@ -21,19 +21,52 @@ namespace rewl {
 // Replica round trips (Sec. 5, Fig. 1): a configuration completes one when it is found in the
 // lowest window after having been found in the highest.  The configurations of both extreme
 // windows are looked at before and after every round (looking twice at one state changes nothing);
-// each configuration sits in one slot, so the threads touch distinct entries.
+// each configuration sits in one slot, so the threads touch distinct entries.  A partitioned handle
+// looks only at the extreme-window slots it hosts (every configuration is hosted by one handle).
 __device__ __forceinline__ void observe_extremes(const ExchangeArgs& a) {
   const int h = a.win.h, m = a.win.m;
   if (h < 2) return;
   for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) {
+    const int g = i < m ? i : (h - 1) * m + (i - m);
+    const int p = a.st.pos_of ? a.st.pos_of[g] : g;
+    if (p < 0) continue;
+    const int r = a.st.perm[p];
     if (i < m) {
-      const int r = a.st.perm[i];
       if (a.st.rt_last[r] == 1) a.st.rt_count[r] += 1;
       a.st.rt_last[r] = 0;
     } else {
-      a.st.rt_last[a.st.perm[(h - 1) * m + (i - m)]] = 1;
+      a.st.rt_last[r] = 1;
     }
   }
+}
+
+__device__ __forceinline__ int position_bin(const ExchangeArgs& a, int p) {
+  return a.traj ? a.st.bin[p] : fx_bin(a.st.efx[p]);
+}
+
+// ln g of the slot at position p at global bin b (window start s), as the 64 bits the tables hold:
+// 2^-40 fixed point (production) or the FP64 bit pattern (trajectory).
+__device__ __forceinline__ long long lng_bits(const ExchangeArgs& a, int p, int b, int s) {
+  const size_t idx = (size_t)p * a.win.W + (b - s);
+  return a.traj ? __double_as_longlong(a.st.lng[idx]) : a.st.lng_fx[idx];
+}
+
+// Eq. 5 from the four ln g values, in one fixed order: D = ((ln g_i(E_A) - ln g_i(E_B)) +
+// ln g_j(E_B)) - ln g_j(E_A), accepted if D >= 0 or u < exp(D).
+__device__ __forceinline__ bool exchange_accepts(const ExchangeArgs& a, long long t, int k, int aa, long long iA,
+                                                 long long iB, long long jB, long long jA) {
+  double D;
+  if (a.traj) {
+    D = __dsub_rn(__dadd_rn(__dsub_rn(__longlong_as_double(iA), __longlong_as_double(iB)), __longlong_as_double(jB)),
+                  __longlong_as_double(jA));
+  } else {
+    const long long Dfx = ((iA - iB) + jB) - jA;
+    D = __dmul_rn(__ll2double_rn(Dfx), kLngUnit);
+  }
+  if (D >= 0.0) return true;
+  const uint4 x = philox10(make_uint4((uint32_t)t, (uint32_t)((unsigned long long)t >> 32), 3u, (uint32_t)aa),
+                           make_uint2((uint32_t)k, a.key1 ^ 0x5eed5eedu));
+  return uniform53(x.x, x.y) < exp_fp64(D, a.ex);
 }
 
 __device__ __forceinline__ void exchange_block(const ExchangeArgs& a) {
@@ -46,42 +79,26 @@ __device__ __forceinline__ void exchange_block(const ExchangeArgs& a) {
   const int parity = (int)(t & 1);
   const int shift = (int)((unsigned long long)(t >> 1) % (unsigned long long)m);
   const int total = ((h - parity) / 2) * m;
+  const bool part = a.st.pos_of != nullptr;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int k = parity + 2 * (idx / m);
     const int aa = idx % m;
     if (k + 1 >= h) continue;
-    const int i = k * m + aa;
-    const int j = (k + 1) * m + (aa + shift) % m;
+    const int gi = k * m + aa;
+    const int gj = (k + 1) * m + (aa + shift) % m;
+    const int i = part ? a.st.pos_of[gi] : gi;      // positions (-1: hosted by another handle)
+    const int j = part ? a.st.pos_of[gj] : gj;
+    if (i < 0 && j < 0) continue;
     const int si = a.win.starts[k], sj = a.win.starts[k + 1];
-    int bA, bB;
-    if (a.traj) {
-      bA = a.st.bin[i];
-      bB = a.st.bin[j];
-    } else {
-      bA = fx_bin(a.st.efx[i]);
-      bB = fx_bin(a.st.efx[j]);
-    }
-    atomicAdd(a.st.ex_att + k, 1ull);
-    if ((unsigned)(bA - sj) >= (unsigned)W || (unsigned)(bB - si) >= (unsigned)W) continue;
-    if ((unsigned)(bA - si) >= (unsigned)W || (unsigned)(bB - sj) >= (unsigned)W) continue;  // defensive
-    double D;
-    if (a.traj) {
-      const double* Li = a.st.lng + (size_t)i * W;
-      const double* Lj = a.st.lng + (size_t)j * W;
-      D = __dsub_rn(__dadd_rn(__dsub_rn(Li[bA - si], Li[bB - si]), Lj[bB - sj]), Lj[bA - sj]);
-    } else {
-      const long long* Li = a.st.lng_fx + (size_t)i * W;
-      const long long* Lj = a.st.lng_fx + (size_t)j * W;
-      const long long Dfx = ((Li[bA - si] - Li[bB - si]) + Lj[bB - sj]) - Lj[bA - sj];
-      D = __dmul_rn(__ll2double_rn(Dfx), kLngUnit);
-    }
-    bool accept = D >= 0.0;
-    if (!accept) {
-      const uint4 x = philox10(make_uint4((uint32_t)t, (uint32_t)((unsigned long long)t >> 32), 3u, (uint32_t)aa),
-                               make_uint2((uint32_t)k, a.key1 ^ 0x5eed5eedu));
-      accept = uniform53(x.x, x.y) < exp_fp64(D, a.ex);
-    }
-    if (accept) {
+    if (i >= 0 && j >= 0) {
+      // both configurations here: swap them between the slots
+      const int bA = position_bin(a, i), bB = position_bin(a, j);
+      atomicAdd(a.st.ex_att + k, 1ull);
+      if ((unsigned)(bA - sj) >= (unsigned)W || (unsigned)(bB - si) >= (unsigned)W) continue;
+      if ((unsigned)(bA - si) >= (unsigned)W || (unsigned)(bB - sj) >= (unsigned)W) continue;  // defensive
+      if (!exchange_accepts(a, t, k, aa, lng_bits(a, i, bA, si), lng_bits(a, i, bB, si), lng_bits(a, j, bB, sj),
+                            lng_bits(a, j, bA, sj)))
+        continue;
       const int32_t tp = a.st.perm[i];
       a.st.perm[i] = a.st.perm[j];
       a.st.perm[j] = tp;
@@ -98,12 +115,63 @@ __device__ __forceinline__ void exchange_block(const ExchangeArgs& a) {
         a.st.efx[j] = te;
       }
       atomicAdd(a.st.ex_acc + k, 1ull);
+    } else {
+      // one side hosted elsewhere: both handles take the same decision from the gathered bins and
+      // ln g values; an accepted swap moves the two slot states between the handles (the caller
+      // moves them), the configurations stay.  The handle hosting slot gi counts the attempt.
+      const int bA = a.part_bin_all[gi], bB = a.part_bin_all[gj];
+      if (i >= 0) atomicAdd(a.st.ex_att + k, 1ull);
+      if ((unsigned)(bA - sj) >= (unsigned)W || (unsigned)(bB - si) >= (unsigned)W) continue;
+      if ((unsigned)(bA - si) >= (unsigned)W || (unsigned)(bB - sj) >= (unsigned)W) continue;  // defensive
+      const long long* L = a.part_lk_all;
+      if (!exchange_accepts(a, t, k, aa, L[2 * gi], L[2 * gi + 1], L[2 * gj], L[2 * gj + 1])) continue;
+      if (i >= 0) {
+        a.part_swap_with[gi] = gj;
+        atomicAdd(a.st.ex_acc + k, 1ull);
+      } else {
+        a.part_swap_with[gj] = gi;
+      }
     }
   }
   __syncthreads();
-  observe_extremes(a);
+  if (!part) observe_extremes(a);   // a partitioned handle looks after the slot states have moved
   if (threadIdx.x == 0) *a.st.ex_index = t + 1;
 }
+
+// Partitioned handles, step 1 of a round: the bin of the configuration at every position, stored at
+// its global slot (bin_all [S_global]; entries of slots hosted elsewhere are left alone).
+__global__ void partition_bins_kernel(const ExchangeArgs a, int n_pos, int32_t* bin_all) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_pos; p += gridDim.x * blockDim.x)
+    bin_all[a.st.gid[p]] = position_bin(a, p);
+}
+
+// Step 2: for every pair of the coming round with exactly one slot here, that slot's ln g at its
+// own configuration's bin and at the partner's (lk [2 S_global]: lk[2 g] and lk[2 g + 1]; 0 when
+// the partner's bin is outside the slot's window, i.e. the pair is rejected anyway).
+__global__ void partition_lookups_kernel(const ExchangeArgs a, const int32_t* bin_all, long long* lk) {
+  const long long t = *a.st.ex_index;
+  const int h = a.win.h, m = a.win.m, W = a.win.W;
+  const int parity = (int)(t & 1);
+  const int shift = (int)((unsigned long long)(t >> 1) % (unsigned long long)m);
+  const int total = ((h - parity) / 2) * m;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int k = parity + 2 * (idx / m);
+    const int aa = idx % m;
+    if (k + 1 >= h) continue;
+    const int gi = k * m + aa;
+    const int gj = (k + 1) * m + (aa + shift) % m;
+    const int i = a.st.pos_of[gi], j = a.st.pos_of[gj];
+    if ((i >= 0) == (j >= 0)) continue;
+    const int g = i >= 0 ? gi : gj, o = i >= 0 ? gj : gi, p = i >= 0 ? i : j;
+    const int s = a.win.starts[g / m];
+    const int bo = bin_all[g], bp = bin_all[o];
+    lk[2 * g] = (unsigned)(bo - s) < (unsigned)W ? lng_bits(a, p, bo, s) : 0;
+    lk[2 * g + 1] = (unsigned)(bp - s) < (unsigned)W ? lng_bits(a, p, bp, s) : 0;
+  }
+}
+
+// After the slot states of a round have moved: the second look at the extreme windows.
+__global__ void partition_observe_kernel(const ExchangeArgs a) { observe_extremes(a); }
 
 __global__ void exchange_kernel(const ExchangeArgs a) { exchange_block(a); }
 
@@ -117,6 +185,21 @@ cudaError_t launch_exchange(const ExchangeArgs& a, cudaStream_t stream) {
 
 cudaError_t launch_exchange_batch(const ExchangeArgs* jobs, int n_jobs, cudaStream_t stream) {
   exchange_batch_kernel<<<n_jobs, 256, 0, stream>>>(jobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_partition_bins(const ExchangeArgs& a, int n_pos, int32_t* bin_all, cudaStream_t stream) {
+  partition_bins_kernel<<<(n_pos + 255) / 256, 256, 0, stream>>>(a, n_pos, bin_all);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_partition_lookups(const ExchangeArgs& a, const int32_t* bin_all, long long* lk, cudaStream_t stream) {
+  partition_lookups_kernel<<<1, 256, 0, stream>>>(a, bin_all, lk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_partition_observe(const ExchangeArgs& a, cudaStream_t stream) {
+  partition_observe_kernel<<<1, 256, 0, stream>>>(a);
   return cudaGetLastError();
 }
 

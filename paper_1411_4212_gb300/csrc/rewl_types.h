@@ -65,7 +65,16 @@ struct WalkerState {
   long long* rt_count;                 // [S] per configuration: round trips completed
   unsigned long long* ex_att;          // [h-1]
   unsigned long long* ex_acc;          // [h-1]
+  // partitioned simulations (one handle per GPU, together one REWL run): the handle's S positions
+  // host global slots; a configuration stays at its position, slot states move between handles
+  const int32_t* gid;                  // [S] global slot hosted at each position (Philox key, window);
+                                       // null: position = global slot
+  const int32_t* pos_of;               // [S_global] position hosting a global slot, -1 elsewhere
+  int S_global;                        // slots of the whole run (h m); S for a plain handle
 };
+
+// Global slot (window k = slot / m, walker a = slot % m) hosted at position p.
+__host__ __device__ __forceinline__ int global_slot(const WalkerState& st, int p) { return st.gid ? st.gid[p] : p; }
 
 struct WalkerArgs {
   Geometry geo;

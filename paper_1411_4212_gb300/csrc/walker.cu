@@ -37,7 +37,7 @@ __device__ void walk(const WalkerArgs& a, int slot, int wlo, typename Mode<kTraj
   const int N = a.geo.N, W = a.win.W;
   const bool bcc = a.geo.kind == 0;
   const bool init = a.init != 0;
-  const uint2 key = make_uint2((uint32_t)slot, a.key1);
+  const uint2 key = make_uint2((uint32_t)global_slot(a.st, slot), a.key1);
 
   // ---- uniform walker state ----
   double E = 0.0;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_kernel(const WalkerArgs
   const int slot = blockIdx.x;
   const int tid = threadIdx.x;
   const int N = a.geo.N, W = a.win.W;
-  const int wlo = a.win.starts[slot / a.win.m];
+  const int wlo = a.win.starts[global_slot(a.st, slot) / a.win.m];
   const int rep = a.st.perm[slot];
 
   Lng* lng_s = reinterpret_cast<Lng*>(smem_raw);

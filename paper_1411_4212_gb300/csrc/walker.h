@@ -46,9 +46,18 @@ struct ExchangeArgs {
   ExpCoeffs ex;
   uint32_t key1;
   int traj;
+  // partitioned handles (st.pos_of set): the round's gathered bins [S_global] and ln g lookups
+  // [2 S_global] of every slot, and the partner of each hosted slot in an accepted cross-handle
+  // swap [S_global] (written only for accepted swaps; the caller presets -1)
+  const int32_t* part_bin_all;
+  const long long* part_lk_all;
+  int32_t* part_swap_with;
 };
 cudaError_t launch_exchange(const ExchangeArgs& a, cudaStream_t stream);
 cudaError_t launch_exchange_batch(const ExchangeArgs* jobs, int n_jobs, cudaStream_t stream);
+cudaError_t launch_partition_bins(const ExchangeArgs& a, int n_pos, int32_t* bin_all, cudaStream_t stream);
+cudaError_t launch_partition_lookups(const ExchangeArgs& a, const int32_t* bin_all, long long* lk, cudaStream_t stream);
+cudaError_t launch_partition_observe(const ExchangeArgs& a, cudaStream_t stream);
 
 struct FlatnessArgs {
   Windows win;

@@ -173,7 +173,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
   const int kBarReady = bar_pair, kBarDone = bar_pair + 2;
   const int warp = tid >> 5, lane = tid & 31;
   const int N = a.geo.N, W = a.win.W, L = a.geo.L;
-  const int wlo = a.win.starts[slot / a.win.m];
+  const int wlo = a.win.starts[global_slot(a.st, slot) / a.win.m];
   const int rep = a.st.perm[slot];
   const uint32_t omask = (uint32_t)a.own_mask;
 
@@ -223,7 +223,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
 
   const int nb = (int)((moves + 31) / 32);
   const long long t0 = a.st.steps[slot];
-  const uint2 key = make_uint2((uint32_t)slot, a.key1);
+  const uint2 key = make_uint2((uint32_t)global_slot(a.st, slot), a.key1);
 
   if (warp == 1) {
     // ------------------------------- producer -------------------------------

@@ -42,6 +42,7 @@ BAD = [
     dict(kind=rw.TABLE, nbr=[[0, 5]], Jt=[[1.0, 1.0]], e_min=-1.0, e_max=1.0),
     dict(kind=rw.TABLE, nbr=[[1, 0]], Jt=[[1.0, 1.0]]),
     dict(kind=7), dict(iteration=2), dict(resolver=4), dict(resolver=-1),
+    dict(partition=(2, 2)), dict(partition=(-1, 2)), dict(partition=(0, 5)), dict(partition=(0, 2), iteration=1),
 ]
 
 

@@ -81,6 +81,8 @@ def test_standalone_exchange_rounds_match_oracle(m):
     for bit, and the stats report the round's attempts and acceptances."""
     gpu, orc = make_pair(L=4, J=(1.0, 0.5), n_bins=200, n_windows=4, walkers_per_window=m, exchange_interval=3000,
                          seed=5, lnf_final=1e-3)
+    gpu.init_walkers()
+    orc.init_walkers()
     gpu.run_intervals(3)
     orc.run_intervals(3)
     for _ in range(8):
