@@ -310,6 +310,30 @@ const char* rewl_last_error(const rewl_handle* h);
 /* Release everything; NULL-safe. */
 void rewl_destroy(rewl_handle* h);
 
+/* ---- Checkpoints ---------------------------------------------------------------------------------
+ * The paper has no checkpoint format; a converged large run takes hours, so the library can stop and
+ * resume one.  A checkpoint holds the whole state of a handle at a call boundary: every
+ * configuration's spins, the slot -> configuration permutation, every walker's energy, ln g and H of
+ * its window, ln f, stage, Philox counter (trial moves done) and counters, the replica-exchange index
+ * and counters, the round-trip records, and for a partitioned handle the global slot of each position.
+ * Resuming from it continues the run exactly: in trajectory mode the resumed run is bit for bit the
+ * uninterrupted one (in production too: the walk is deterministic for given arguments).  The
+ * buffer is host memory of rewl_state_bytes bytes, about the size of the spins (production: 16 N bytes
+ * per walker; trajectory: 24 N). */
+
+/* Size in bytes of the handle's checkpoint. */
+rewl_status rewl_state_bytes(rewl_handle* h, int64_t* bytes);
+
+/* Write the checkpoint into buf (host, `bytes` = rewl_state_bytes, else REWL_EINVAL).  Blocks. */
+rewl_status rewl_save_state(rewl_handle* h, void* buf, int64_t bytes);
+
+/* Replace the handle's state by a checkpoint.  The handle must have been created with the same lattice,
+ * couplings, windows, walkers, overlap, flatness, ln f_final, seed, mode, group size, exchange interval,
+ * recomputation cadence, iteration reading and partition range as the one that saved it.  REWL_EINVAL, with
+ * the handle unchanged, when the size, tag or version differ, when the checksum (64-bit FNV-1a over the
+ * buffer) does not match (a corrupted buffer), or when the run's arguments differ.  Blocks. */
+rewl_status rewl_load_state(rewl_handle* h, const void* buf, int64_t bytes);
+
 /* ---- Partitioned runs: one REWL run split over several handles (one per GPU) -------------------
  * The paper runs every walker as its own process and exchanges replicas between processes of
  * adjacent windows (Sec. 4.3, Eq. 5).  Here a run of h windows x m walkers can be split over handles

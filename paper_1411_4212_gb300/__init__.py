@@ -141,6 +141,9 @@ def load_library(path=LIB_PATH):
         "rewl_thermo": ([_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, _vp, _vp, _vp], st),
         "rewl_set_initial_lng": ([_vp, _vp, C.c_double], st),
         "rewl_peak_temperature": ([_vp, _vp, C.c_int, C.POINTER(C.c_double), _vp], st),
+        "rewl_state_bytes": ([_vp, C.POINTER(C.c_int64)], st),
+        "rewl_save_state": ([_vp, _vp, C.c_int64], st),
+        "rewl_load_state": ([_vp, _vp, C.c_int64], st),
         "rewl_create_partition": ([C.POINTER(Lattice), C.POINTER(Couplings), C.POINTER(Windows), C.c_int, C.c_double,
                                    C.c_double, C.c_double, C.POINTER(Config), C.c_int, C.c_int, C.POINTER(_vp)], st),
         "rewl_partition_slots": ([_vp, _vp], st),
@@ -417,6 +420,23 @@ class REWL:
 
     def centres(self):
         return self.e_min + (np.arange(self.B) + 0.5) * self.dE
+
+    # -- checkpoints -------------------------------------------------------------------------
+    def save_state(self, path=None):
+        """The handle's checkpoint as a uint8 array (written to `path` as well when given)."""
+        n = C.c_int64()
+        _check(self._lib.rewl_state_bytes(self._h, C.byref(n)), self._h)
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(self._lib.rewl_save_state(self._h, _ptr(buf), buf.size), self._h)
+        if path is not None:
+            buf.tofile(path)
+        return buf
+
+    def load_state(self, src):
+        """Resume from a checkpoint (a save_state array, or the path of a file it was written to)."""
+        buf = np.fromfile(src, dtype=np.uint8) if isinstance(src, (str, os.PathLike)) else \
+            np.ascontiguousarray(src, dtype=np.uint8)
+        _check(self._lib.rewl_load_state(self._h, _ptr(buf), buf.size), self._h)
 
     # -- partitioned runs (see partition.py for the round protocol) -------------------------
     @property

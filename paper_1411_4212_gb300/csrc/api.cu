@@ -1571,6 +1571,157 @@ rewl_status rewl_slot_import(rewl_handle* h, int32_t g_out, const void* buf) {
   return REWL_OK;
 }
 
+// ---- checkpoints --------------------------------------------------------------------------------
+// Layout: header (tag, version, total bytes, fingerprint of the run's arguments, host counters),
+// then every device state array in a fixed order, then a checksum of everything before it.
+constexpr unsigned long long kCkptTag = 0x5245574c434b5054ULL;   // "REWLCKPT"
+constexpr long long kCkptVersion = 1;
+constexpr int kCkptHead = 10;   // int64 words
+
+struct Section {
+  void* dev;
+  size_t bytes;
+};
+
+static std::vector<Section> state_sections(rewl_handle* h) {
+  const size_t S = h->S, W = h->W, N = h->N, X = (size_t)std::max(h->h - 1, 1);
+  std::vector<Section> v;
+  v.push_back({h->d_spins, h->traj ? S * 3 * N * sizeof(double) : S * N * sizeof(float4)});
+  v.push_back({h->d_perm, S * 4});
+  v.push_back({h->d_H, S * W * 4});
+  if (h->traj) {
+    v.push_back({h->d_lng, S * W * 8});
+    v.push_back({h->d_E, S * 8});
+    v.push_back({h->d_bin, S * 4});
+  } else {
+    v.push_back({h->d_lng_fx, S * W * 8});
+    v.push_back({h->d_efx, S * 8});
+    v.push_back({h->d_lnf_fx, S * 8});
+  }
+  v.push_back({h->d_lnf, S * 8});
+  v.push_back({h->d_stage, S * 4});
+  v.push_back({h->d_steps, S * 8});
+  v.push_back({h->d_accepts, S * 8});
+  v.push_back({h->d_recomputes, S * 8});
+  v.push_back({h->d_path_batches, 3 * S * 8});
+  v.push_back({h->d_init_moves, S * 8});
+  v.push_back({h->d_drift, S * 8});
+  v.push_back({h->d_ex_index, 8});
+  v.push_back({h->d_rt_last, S * 4});
+  v.push_back({h->d_rt_count, S * 8});
+  v.push_back({h->d_ex_att, X * 8});
+  v.push_back({h->d_ex_acc, X * 8});
+  if (h->part) {
+    v.push_back({h->d_gid, S * 4});
+    v.push_back({h->d_pos_of, (size_t)h->S_global * 4});
+  }
+  return v;
+}
+
+static size_t state_bytes(rewl_handle* h) {
+  size_t b = kCkptHead * 8;
+  for (const Section& x : state_sections(h)) b += (x.bytes + 7) & ~(size_t)7;
+  return b + 8;
+}
+
+// 64-bit FNV-1a over 8-byte words (the buffer length is a multiple of 8).
+static unsigned long long ckpt_hash(const unsigned char* p, size_t n) {
+  unsigned long long x = 0xcbf29ce484222325ULL;
+  for (size_t i = 0; i < n; i += 8) {
+    unsigned long long w;
+    std::memcpy(&w, p + i, 8);
+    x = (x ^ w) * 0x100000001b3ULL;
+  }
+  return x;
+}
+
+// What must agree between the handle that saved a checkpoint and the one that loads it.
+static unsigned long long run_fingerprint(const rewl_handle* h) {
+  std::vector<unsigned long long> f;
+  auto d = [&](double v) {
+    unsigned long long w;
+    std::memcpy(&w, &v, 8);
+    f.push_back(w);
+  };
+  for (long long v : {(long long)h->kind, (long long)h->L, (long long)h->N, (long long)h->z, (long long)h->B,
+                      (long long)h->h, (long long)h->m, (long long)h->W, (long long)h->S, (long long)h->traj,
+                      (long long)h->G, (long long)h->exchange_interval, (long long)h->recompute_every,
+                      (long long)h->by_window, (long long)h->part, (long long)h->k_begin, (long long)h->k_end,
+                      (long long)h->geo.n_shells})
+    f.push_back((unsigned long long)v);
+  f.push_back(h->seed);
+  for (double v : {h->e_min, h->e_max, h->overlap, h->flatness, h->lnf_final}) d(v);
+  for (int j = 0; j < 4; ++j) d(h->geo.Jsh_d[j]);
+  for (double v : h->tab_J) d(v);
+  for (int32_t v : h->tab_nbr) f.push_back((unsigned long long)(uint32_t)v);
+  return ckpt_hash(reinterpret_cast<const unsigned char*>(f.data()), f.size() * 8);
+}
+
+rewl_status rewl_state_bytes(rewl_handle* h, int64_t* bytes) {
+  rewl_status s = check_ready(h);
+  if (s != REWL_OK) return s;
+  if (!bytes) return fail(h, REWL_EINVAL, "bytes is NULL");
+  *bytes = (int64_t)state_bytes(h);
+  return REWL_OK;
+}
+
+rewl_status rewl_save_state(rewl_handle* h, void* buf, int64_t bytes) {
+  rewl_status s = check_ready(h);
+  if (s != REWL_OK) return s;
+  const size_t n = state_bytes(h);
+  if (!buf || bytes != (int64_t)n) return fail(h, REWL_EINVAL, "buffer must hold rewl_state_bytes bytes");
+  unsigned char* p = static_cast<unsigned char*>(buf);
+  long long head[kCkptHead] = {(long long)kCkptTag, kCkptVersion, (long long)n, (long long)run_fingerprint(h),
+                               h->initialized ? 1 : 0, h->intervals_done, h->prev_accepts, (long long)h->prev_ex_att,
+                               (long long)h->prev_ex_acc, 0};
+  std::memcpy(p, head, sizeof head);
+  size_t off = sizeof head;
+  for (const Section& x : state_sections(h)) {
+    CUDA_TRY(h, cudaMemcpyAsync(p + off, x.dev, x.bytes, cudaMemcpyDeviceToHost, h->stream));
+    const size_t pad = ((x.bytes + 7) & ~(size_t)7) - x.bytes;
+    if (pad) std::memset(p + off + x.bytes, 0, pad);
+    off += x.bytes + pad;
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  const unsigned long long c = ckpt_hash(p, off);
+  std::memcpy(p + off, &c, 8);
+  return REWL_OK;
+}
+
+rewl_status rewl_load_state(rewl_handle* h, const void* buf, int64_t bytes) {
+  rewl_status s = check_ready(h);
+  if (s != REWL_OK) return s;
+  const size_t n = state_bytes(h);
+  if (!buf || bytes != (int64_t)n) return fail(h, REWL_EINVAL, "checkpoint size does not match this handle");
+  const unsigned char* p = static_cast<const unsigned char*>(buf);
+  long long head[kCkptHead];
+  std::memcpy(head, p, sizeof head);
+  unsigned long long c;
+  std::memcpy(&c, p + n - 8, 8);
+  if ((unsigned long long)head[0] != kCkptTag || head[1] != kCkptVersion || head[2] != (long long)n)
+    return fail(h, REWL_EINVAL, "not a checkpoint of this library version and size");
+  if (ckpt_hash(p, n - 8) != c) return fail(h, REWL_EINVAL, "checkpoint checksum mismatch (corrupted)");
+  if ((unsigned long long)head[3] != run_fingerprint(h))
+    return fail(h, REWL_EINVAL, "checkpoint of a run created with other arguments");
+  size_t off = kCkptHead * 8;
+  for (const Section& x : state_sections(h)) {
+    CUDA_TRY(h, cudaMemcpyAsync(x.dev, p + off, x.bytes, cudaMemcpyHostToDevice, h->stream));
+    off += (x.bytes + 7) & ~(size_t)7;
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->initialized = head[4] != 0;
+  h->intervals_done = head[5];
+  h->prev_accepts = head[6];
+  h->prev_ex_att = (unsigned long long)head[7];
+  h->prev_ex_acc = (unsigned long long)head[8];
+  if (h->part) {
+    CUDA_TRY(h, cudaMemcpy(h->gid_host.data(), h->d_gid, h->S * 4, cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(h->pos_host.data(), h->d_pos_of, (size_t)h->S_global * 4, cudaMemcpyDeviceToHost));
+  }
+  h->wargs_valid = false;
+  return REWL_OK;
+}
+
 rewl_status rewl_device_exp(const double* x, double* y, int n) {
   if (!x || !y || n < 0) return fail(nullptr, REWL_EINVAL, "bad arguments");
   if (n == 0) return REWL_OK;

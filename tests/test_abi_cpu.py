@@ -82,3 +82,7 @@ def test_batch_entry_points_reject_invalid_arguments():
     lib.rewl_batch_destroy(None)
     t = C.c_double()
     assert lib.rewl_peak_temperature(None, None, 0, C.byref(t), None) == rw.EINVAL
+    n = C.c_int64()
+    assert lib.rewl_state_bytes(None, C.byref(n)) == rw.EINVAL
+    assert lib.rewl_save_state(None, None, 0) == rw.EINVAL and lib.rewl_load_state(None, None, 0) == rw.EINVAL
+    assert lib.rewl_slot_export(None, 0, None) == rw.EINVAL and lib.rewl_partition_observe(None) == rw.EINVAL
