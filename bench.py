@@ -604,8 +604,8 @@ def main():
 
     # roofline of the walker kernel: lattices in shared memory against the shared-memory bandwidth
     # of this GPU (neighbour spins, ln g and H, records); lattices in global memory against HBM
-    # (the lattice bytes alone: FP32 components of the z neighbours and the old spin, the accepted
-    # new spin written back)
+    # (the lattice bytes alone: the 8-byte spin codes of the z neighbours and the old spin, the
+    # accepted new spin written back)
     z = sim.z
     walk_avg_ms = statistics.mean(walk_ms)
     walker_share = sum(walk_ms) / sum(step_ms)
@@ -613,12 +613,12 @@ def main():
     in_smem = "true" if sim.info()["lattice_in_shared"] else "false"
     if in_smem == "true":
         bound = "smem"
-        bytes_per_move = 12 * z + 12 + 2 * 8 + 8 + 4 + 12 * acc_rate
+        bytes_per_move = 8 * z + 8 + 2 * 8 + 8 + 4 + 8 * acc_rate
         peak, _ = rw.measure_smem_bandwidth(stream)
         peak_source = "measured live: conflict-free 16-byte shared-memory loads on every SM"
     else:
         bound = "hbm"
-        bytes_per_move = 12 * z + 12 + 12 * acc_rate
+        bytes_per_move = 8 * z + 8 + 8 * acc_rate
         peak, peak_source = hbm_peak()
     achieved = bytes_per_move * S * workload["exchange_interval"] / (walk_avg_ms * 1e-3)
     nsh = len(workload["J"])

@@ -577,8 +577,8 @@ static rewl_status create_impl(const rewl_lattice* lat, const rewl_couplings* cp
   auto A = [&](auto** p, size_t count) {
     if (st == REWL_OK) st = dev_alloc(h, p, count);
   };
-  // spins: FP64 planes [S][3][N] (trajectory) or FP32 quads (x, y, z, 0) [S][N] (production)
-  const size_t spin_bytes = h->traj ? S * 3 * N * sizeof(double) : S * N * sizeof(float4);
+  // spins: FP64 planes [S][3][N] (trajectory) or octahedral FP32 codes [S][N] float2 (production)
+  const size_t spin_bytes = h->traj ? S * 3 * N * sizeof(double) : S * N * sizeof(float2);
   void** spins_pp = &h->d_spins;
   {
     unsigned char* sp = nullptr;
@@ -642,20 +642,15 @@ static rewl_status create_impl(const rewl_lattice* lat, const rewl_couplings* cp
   auto zero = [&](void* d, size_t bytes) {
     if (ce == cudaSuccess) ce = cudaMemset(d, 0, bytes);
   };
-  {
-    // every configuration starts aligned along z
+  // every configuration starts aligned along +z: FP64 planes with z = 1, or the code (0, 0)
+  if (h->traj) {
     std::vector<unsigned char> sp(spin_bytes, 0);
+    const double one = 1.0;
     for (size_t r = 0; r < S; ++r)
-      for (size_t i = 0; i < N; ++i) {
-        if (h->traj) {
-          const double one = 1.0;
-          std::memcpy(sp.data() + (r * 3 * N + 2 * N + i) * sizeof(double), &one, sizeof one);
-        } else {
-          const float one = 1.0f;
-          std::memcpy(sp.data() + ((r * N + i) * 4 + 2) * sizeof(float), &one, sizeof one);
-        }
-      }
+      for (size_t i = 0; i < N; ++i) std::memcpy(sp.data() + (r * 3 * N + 2 * N + i) * sizeof(double), &one, sizeof one);
     up(h->d_spins, sp.data(), sp.size());
+  } else {
+    zero(h->d_spins, spin_bytes);
   }
   std::vector<int32_t> perm(S);
   for (size_t s = 0; s < S; ++s) perm[s] = (int32_t)s;
@@ -1290,14 +1285,15 @@ rewl_status rewl_get_spins(rewl_handle* h, double* spins) {
     CUDA_TRY(h, cudaMemcpyAsync(spins, h->d_spins, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   } else {
-    // device quads (x, y, z, 0) per site -> host planes
-    const size_t N = h->N, R = h->S;
-    std::vector<float> t(R * N * 4);
-    CUDA_TRY(h, cudaMemcpyAsync(t.data(), h->d_spins, t.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    // device codes -> the FP32 spins the walkers see (decoded on the device) -> host FP64 planes
+    float* d = nullptr;
+    std::vector<float> t(n);
+    CUDA_TRY(h, cudaMallocAsync(&d, n * sizeof(float), h->stream));
+    CUDA_TRY(h, launch_decode_spins(static_cast<const float2*>(h->d_spins), (size_t)h->S, h->N, d, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(t.data(), d, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaFreeAsync(d, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    for (size_t r = 0; r < R; ++r)
-      for (size_t c = 0; c < 3; ++c)
-        for (size_t i = 0; i < N; ++i) spins[(r * 3 + c) * N + i] = t[(r * N + i) * 4 + c];
+    for (size_t i = 0; i < n; ++i) spins[i] = t[i];
   }
   return REWL_OK;
 }
@@ -1586,7 +1582,7 @@ struct Section {
 static std::vector<Section> state_sections(rewl_handle* h) {
   const size_t S = h->S, W = h->W, N = h->N, X = (size_t)std::max(h->h - 1, 1);
   std::vector<Section> v;
-  v.push_back({h->d_spins, h->traj ? S * 3 * N * sizeof(double) : S * N * sizeof(float4)});
+  v.push_back({h->d_spins, h->traj ? S * 3 * N * sizeof(double) : S * N * sizeof(float2)});
   v.push_back({h->d_perm, S * 4});
   v.push_back({h->d_H, S * W * 4});
   if (h->traj) {

@@ -88,6 +88,37 @@ __device__ __forceinline__ void unpack_offset(uint32_t p, int& dx, int& dy, int&
   dz = (int)((p >> 16) & 0xffu) - 8;
 }
 
+// Production spins are stored as two FP32 octahedral coordinates, 8 bytes per site.  A unit vector s
+// is projected to p = s / (|x| + |y| + |z|) on the octahedron |x| + |y| + |z| = 1.  Its upper half
+// (z >= 0) is kept as (u, v) = (p_x, p_y); its lower half is folded over the square's edges,
+// (u, v) = ((1 - |p_y|) sign p_x, (1 - |p_x|) sign p_y).  Decoding undoes the fold
+// (z = 1 - |u| - |v|; for z < 0 x and y move towards 0 by -z) and normalises.  The grid is about
+// 1e-7 rad fine everywhere (FP32 spacing of u and v), the resolution of FP32 components.
+// Every proposed spin goes through encode and decode before its energy change is taken, and the code
+// is what the lattice stores, so the lattice always holds exactly the spin the energy saw.
+__device__ __forceinline__ float2 oct_encode(float x, float y, float z) {
+  const float s = __fdiv_rn(1.0f, fabsf(x) + fabsf(y) + fabsf(z));
+  float u = x * s, v = y * s;
+  if (z < 0.0f) {
+    const float fu = copysignf(1.0f - fabsf(v), u);
+    const float fv = copysignf(1.0f - fabsf(u), v);
+    u = fu;
+    v = fv;
+  }
+  return make_float2(u, v);
+}
+
+__device__ __forceinline__ void oct_decode(float2 c, float& x, float& y, float& z) {
+  z = 1.0f - fabsf(c.x) - fabsf(c.y);
+  const float t = fmaxf(-z, 0.0f);
+  x = c.x >= 0.0f ? c.x - t : c.x + t;
+  y = c.y >= 0.0f ? c.y - t : c.y + t;
+  const float r = rsqrtf(fmaf(x, x, fmaf(y, y, z * z)));
+  x *= r;
+  y *= r;
+  z *= r;
+}
+
 // Fixed-point scales of the production mode.
 //  energy: int64 in units of 2^-32 bins above e_min, so the bin index is the high 32-bit word;
 //  ln g, ln f, ln u: int64 in units of 2^-40.

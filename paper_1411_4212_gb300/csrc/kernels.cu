@@ -585,6 +585,24 @@ cudaError_t launch_peak(const double* T, const double* C, int nT, double* out, c
   return cudaGetLastError();
 }
 
+// Production lattices: the octahedral codes [R][N] decoded to FP32 planes [R][3][N].
+__global__ void decode_spins_kernel(const float2* c, size_t R, int N, float* out) {
+  const size_t n = R * (size_t)N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = i / (size_t)N, k = i % (size_t)N;
+    float x, y, z;
+    oct_decode(c[i], x, y, z);
+    out[(r * 3 + 0) * N + k] = x;
+    out[(r * 3 + 1) * N + k] = y;
+    out[(r * 3 + 2) * N + k] = z;
+  }
+}
+
+cudaError_t launch_decode_spins(const float2* codes, size_t R, int N, float* out, cudaStream_t stream) {
+  decode_spins_kernel<<<1024, 256, 0, stream>>>(codes, R, N, out);
+  return cudaGetLastError();
+}
+
 __global__ void device_exp_kernel(const double* x, double* y, int n, const ExpCoeffs c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = exp_fp64(x[i], c);

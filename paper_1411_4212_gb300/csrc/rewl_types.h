@@ -41,7 +41,7 @@ struct Windows {
 };
 
 struct WalkerState {
-  void* spins;                         // [R][N] float4 (x, y, z, 0) (production) or [R][3][N] double (trajectory)
+  void* spins;                         // [R][N] float2 octahedral codes (production) or [R][3][N] double (trajectory)
   int32_t* perm;                       // [S] configuration held by slot s
   uint32_t* H;                         // [S][W]
   long long* lng_fx;                   // production [S][W], 2^-40 units

@@ -87,6 +87,7 @@ __device__ void walk(const WalkerArgs& a, int slot, int wlo, typename Mode<kTraj
     Real nx, ny, nz;
     double u = 0.0;
     long long lu = 0;
+    float2 code = make_float2(0.0f, 0.0f);
     const unsigned long long tk = (unsigned long long)(t + g);
     if (kTraj) {
       double dnx, dny, dnz;
@@ -97,6 +98,8 @@ __device__ void walk(const WalkerArgs& a, int slot, int wlo, typename Mode<kTraj
     } else {
       float fnx, fny, fnz;
       draw_prod(key, tk, init, N, site, lu, fnx, fny, fnz);
+      code = oct_encode(fnx, fny, fnz);        // the proposal is the spin its code decodes to
+      oct_decode(code, fnx, fny, fnz);
       nx = (Real)fnx;
       ny = (Real)fny;
       nz = (Real)fnz;
@@ -230,7 +233,7 @@ __device__ void walk(const WalkerArgs& a, int slot, int wlo, typename Mode<kTraj
       if (acc) {
         acc_mask |= 1u << k;
         ++n_acc;
-        if (lane == src) lat.set(site, nx, ny, nz);
+        if (lane == src) put_spin(lat, site, nx, ny, nz, code);
         __syncwarp();
       }
       if (!init && !frozen) {
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(kWalkerThreads) walker_kernel(const WalkerArgs
   const auto glat = GlobalLattice<kTraj>::of(a.st.spins, rep, N);
   typename WalkLattice<kTraj, kSmem>::T lat;
   if constexpr (kSmem)
-    lat = SpinPlanes<Real>(spin_s, N);
+    lat = typename WalkLattice<kTraj, true>::T(spin_s, N);
   else
     lat = glat;
 
@@ -395,7 +398,7 @@ size_t walker_smem_bytes(bool traj, bool smem_lattice, int N, int W) {
   const size_t h = ((size_t)W * 4 + 15) & ~(size_t)15;
   const size_t real = traj ? sizeof(double) : sizeof(float);
   size_t bytes = lng + h + 4 * kMaxSlotsPerSite + real * kMaxSlotsPerSite;
-  if (smem_lattice) bytes += real * 3 * (size_t)N;
+  if (smem_lattice) bytes += smem_site_bytes(traj) * (size_t)N;
   return bytes;
 }
 

@@ -87,6 +87,8 @@ cudaError_t launch_merge(const MergeArgs& a, cudaStream_t stream);
 cudaError_t launch_thermo(const double* lng, const double* E, int B, double n_spins, const double* T, int nT,
                           double* U, double* C, double* lnZ, cudaStream_t stream);
 
+cudaError_t launch_decode_spins(const float2* codes, size_t R, int N, float* out, cudaStream_t stream);
+
 cudaError_t launch_peak(const double* T, const double* C, int nT, double* out, cudaStream_t stream);
 
 cudaError_t launch_device_exp(const double* x, double* y, int n, const ExpCoeffs& c, cudaStream_t stream);

@@ -2,6 +2,8 @@
 // change of a trial move, FP64 binning, the trial-move draws of both modes, and the full energy.
 #pragma once
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "walker.h"
 
@@ -20,11 +22,14 @@ struct Mode<false> {
   using Lng = long long;
 };
 
-// Spins of one configuration, in one of two layouts.
-// SpinPlanes: three arrays x[N], y[N], z[N] -- lattices in shared memory, and FP64 lattices in global
-//   memory ([R][3][N]).
-// SpinQuads: one (x, y, z, 0) float4 per site -- FP32 lattices in global memory ([R][N]): a
-//   neighbour's spin is one 16-byte load from one 32-byte sector instead of three loads from three.
+// Spins of one configuration.
+// SpinPlanes: three FP64 arrays x[N], y[N], z[N] -- trajectory lattices, in global memory ([R][3][N])
+//   and in shared memory.
+// SpinCodes: one float2 octahedral code per site -- production lattices in global memory ([R][N]): a
+//   neighbour's spin is one 8-byte load, and eight sites share a 64-byte DRAM access.
+// CodePlanes: the same codes as two FP32 arrays u[N], v[N] -- production lattices in shared memory.
+// get() returns the spin (decoded in production); trajectory lattices are written with set(x, y, z),
+// production lattices with set_code(code).
 template <typename Real>
 struct SpinPlanes {
   using Value = Real;
@@ -43,21 +48,30 @@ struct SpinPlanes {
   }
 };
 
-struct SpinQuads {
+struct SpinCodes {
   using Value = float;
-  float4* q;
+  float2* c;
+  __device__ __forceinline__ void get(int i, float& vx, float& vy, float& vz) const { oct_decode(c[i], vx, vy, vz); }
+  __device__ __forceinline__ float2 get_code(int i) const { return c[i]; }
+  __device__ __forceinline__ void set_code(int i, float2 v) const { c[i] = v; }
+};
+
+struct CodePlanes {
+  using Value = float;
+  float *u, *v;
+  __device__ __forceinline__ CodePlanes() : u(nullptr), v(nullptr) {}
+  __device__ __forceinline__ CodePlanes(float* p, int N) : u(p), v(p + N) {}
   __device__ __forceinline__ void get(int i, float& vx, float& vy, float& vz) const {
-    const float4 v = q[i];
-    vx = v.x;
-    vy = v.y;
-    vz = v.z;
+    oct_decode(make_float2(u[i], v[i]), vx, vy, vz);
   }
-  __device__ __forceinline__ void set(int i, float vx, float vy, float vz) const {
-    q[i] = make_float4(vx, vy, vz, 0.0f);
+  __device__ __forceinline__ float2 get_code(int i) const { return make_float2(u[i], v[i]); }
+  __device__ __forceinline__ void set_code(int i, float2 w) const {
+    u[i] = w.x;
+    v[i] = w.y;
   }
 };
 
-// The global-memory lattice of configuration r: FP64 planes (trajectory) or FP32 quads (production).
+// The global-memory lattice of configuration r: FP64 planes (trajectory) or codes (production).
 template <bool kTraj>
 struct GlobalLattice {
   using T = SpinPlanes<double>;
@@ -67,30 +81,52 @@ struct GlobalLattice {
 };
 template <>
 struct GlobalLattice<false> {
-  using T = SpinQuads;
+  using T = SpinCodes;
   static __device__ __forceinline__ T of(void* spins, int r, int N) {
-    return SpinQuads{reinterpret_cast<float4*>(spins) + (size_t)r * N};
+    return SpinCodes{reinterpret_cast<float2*>(spins) + (size_t)r * N};
   }
 };
 
-// The lattice a walker reads: planes in shared memory, else the global layout of its mode.
+// The lattice a walker reads: its mode's shared-memory layout, else its global layout.
 template <bool kTraj, bool kSmem>
 struct WalkLattice {
-  using T = SpinPlanes<typename Mode<kTraj>::Real>;
+  using T = SpinPlanes<double>;
+};
+template <>
+struct WalkLattice<false, true> {
+  using T = CodePlanes;
 };
 template <bool kTraj>
 struct WalkLattice<kTraj, false> {
   using T = typename GlobalLattice<kTraj>::T;
 };
 
-// Copy N spins between layouts by the nt threads t of a group.
-template <class Dst, class Src>
-__device__ __forceinline__ void copy_lattice(const Dst& d, const Src& s, int N, int t, int nt) {
+// Bytes per site of a lattice in shared memory.
+__host__ __device__ constexpr size_t smem_site_bytes(bool traj) { return traj ? 3 * sizeof(double) : 2 * sizeof(float); }
+
+// Copy N spins between a global and a shared-memory lattice by the nt threads t of a group (production
+// copies the codes, so a spin never changes on the way).
+__device__ __forceinline__ void copy_lattice(const SpinPlanes<double>& d, const SpinPlanes<double>& s, int N, int t,
+                                             int nt) {
   for (int i = t; i < N; i += nt) {
-    typename Src::Value vx, vy, vz;
+    double vx, vy, vz;
     s.get(i, vx, vy, vz);
     d.set(i, vx, vy, vz);
   }
+}
+template <class Dst, class Src>
+__device__ __forceinline__ void copy_lattice(const Dst& d, const Src& s, int N, int t, int nt) {
+  for (int i = t; i < N; i += nt) d.set_code(i, s.get_code(i));
+}
+
+// Write spin (x, y, z) with production code c at site i (trajectory lattices take the components,
+// production lattices the code).
+template <class Lat, typename Real>
+__device__ __forceinline__ void put_spin(const Lat& lat, int i, Real x, Real y, Real z, float2 c) {
+  if constexpr (std::is_same<Lat, SpinPlanes<double>>::value)
+    lat.set(i, x, y, z);
+  else
+    lat.set_code(i, c);
 }
 
 __device__ __forceinline__ long long shfl_ll(long long v, int src) {

@@ -72,7 +72,7 @@ struct alignas(16) Rec<false> {
   float ox, oy, oz;      // spin at the site before the move (snapshot, corrected by the resolver)
   float hx, hy, hz;      // local field (snapshot, corrected by the resolver)
   float dsx, dsy, dsz;   // new - old spin: the move's change to the lattice if accepted
-  int pad[2];
+  float cu, cv;          // octahedral code of the proposed spin (what the lattice stores)
 };
 template <>
 struct alignas(16) Rec<true> {
@@ -201,7 +201,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
   const auto glat = GlobalLattice<kTraj>::of(a.st.spins, rep, N);
   typename WalkLattice<kTraj, kSmem>::T lat;
   if constexpr (kSmem)
-    lat = SpinPlanes<Real>(spin_s, N);
+    lat = typename WalkLattice<kTraj, true>::T(spin_s, N);
   else
     lat = glat;
 
@@ -241,6 +241,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       Real nx, ny, nz;
       double u = 0.0;
       int lu = 0;
+      float2 code = make_float2(0.0f, 0.0f);
       if constexpr (kTraj) {
         double dnx, dny, dnz;
         draw_traj(key, t, false, N, site, u, dnx, dny, dnz);
@@ -257,9 +258,13 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         __sincosf((one_to_two(x.w) - 1.5f) * 6.28318530717958648f, &sn, &cs);  // azimuth in [-pi, pi)
         const float q = fmaxf(fmaf(-zc, zc, 1.0f), 0x1.0p-46f);
         const float r = q * rsqrtf(q);                                          // sin(theta)
-        nx = (Real)(r * cs);
-        ny = (Real)(r * sn);
-        nz = (Real)zc;
+        // the proposal is the spin its code decodes to
+        code = oct_encode(r * cs, r * sn, zc);
+        float fx, fy, fz;
+        oct_decode(code, fx, fy, fz);
+        nx = (Real)fx;
+        ny = (Real)fy;
+        nz = (Real)fz;
       }
       int X, Y, Z;
       bcc_coords(site, L, a.geo.divL, X, Y, Z);
@@ -294,6 +299,8 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         r.dsx = dx;
         r.dsy = dy;
         r.dsz = dz;
+        r.cu = code.x;
+        r.cv = code.y;
       }
       r.cprev = b > 0 ? oprev : 0u;
       r.ccur = ocur & ((1u << lane) - 1u);
@@ -552,7 +559,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
     auto publish = [&](const Rec<false>* R, uint32_t acc) {
       if ((acc >> lane) & 1u) {
         const Rec<false>& rp = R[lane];
-        lat.set(rp.site, rp.nx, rp.ny, rp.nz);
+        lat.set_code(rp.site, make_float2(rp.cu, rp.cv));
       }
       __syncwarp();
     };
@@ -1009,7 +1016,7 @@ size_t walker_pipe_smem_bytes(bool traj, bool smem_lattice, int N, int W, int ow
   const size_t real = traj ? sizeof(double) : sizeof(float);
   const size_t recs = (traj ? sizeof(Rec<true>) : sizeof(Rec<false>)) * 64 + sizeof(int4) * 64 + sizeof(uint32_t) * 32;
   size_t bytes = lng + h + 4 * kMaxSlotsPerSite + real * kMaxSlotsPerSite + recs + 8 * (size_t)own_entries;
-  if (smem_lattice) bytes += real * 3 * (size_t)N;
+  if (smem_lattice) bytes += smem_site_bytes(traj) * (size_t)N;
   return bytes;
 }
 

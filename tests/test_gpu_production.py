@@ -180,11 +180,11 @@ def test_large_four_shell_geometry_global_path():
 
 @pytest.mark.parametrize("placement", ["shared", "global"])
 def test_production_spins_read_back_as_the_device_holds_them(placement):
-    """Production spins live on the device as (x, y, z, 0) FP32 quads, copied into shared-memory
-    planes by the walker when the lattice fits there (placement "global" keeps it in place through a
-    one-job batch).  rewl_get_spins returns FP64 planes [R][3][N]: they start along +z, stay unit
-    vectors, and the energy computed on the host from them and the library's neighbour table equals
-    the device's own recomputation for every configuration."""
+    """Production spins live on the device as two FP32 octahedral coordinates per site.  The walker
+    copies the codes into shared memory when the lattice fits there; placement "global" keeps them in
+    place through a one-job batch.  rewl_get_spins returns the decoded spins as FP64 planes [R][3][N].
+    They start along +z and stay unit vectors.  The energy computed on the host from them and the
+    library's neighbour table equals the device's own recomputation for every configuration."""
     g = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, L=6, J=(1.0, 0.5, 0.1), n_bins=300, n_windows=3,
                 walkers_per_window=2, seed=4, exchange_interval=3000, group_size=1)
     sp0 = g.spins()
