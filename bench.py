@@ -61,11 +61,21 @@ def parse():
     p.add_argument("--jobs-per-size", type=int, default=16,
                    help="batch64: jobs per lattice size (16 gives the 64-job workload; smaller for profiling)")
     p.add_argument("--workload", default="large",
-                   choices=["large", "cfg2", "batch64", "warmstart", "weak-scaling"],
+                   choices=["large", "cfg2", "batch64", "warmstart", "weak-scaling", "target"],
                    help="large: one job, bcc L=32 with four shells, 64 windows x 8 walkers (the headline "
                         "line); cfg2: one job, bcc L=16 with two shells, 16 windows x 4 walkers; batch64: 64 "
                         "jobs of bcc L=8..20 in one persistent launch; warmstart: learned warm start versus "
-                        "plain REWL; weak-scaling: moves to finish the first WL iteration versus L")
+                        "plain REWL; weak-scaling: moves to finish the first WL iteration versus L; target: "
+                        "bcc L=32 four-shell couplings converged, warm start against plain")
+    p.add_argument("--ws-sizes", default="4,6,8,10,16,20,30,40,50",
+                   help="weak-scaling: bcc L of the windowed jobs (the paper's Fig. 3 covers L = 10..50)")
+    p.add_argument("--target-lnf", type=float, default=1e-8, help="target: ln f_final of the plain and warm runs")
+    p.add_argument("--target-replicas", type=int, default=2, help="target: plain and warm runs each")
+    p.add_argument("--target-refs", type=int, default=2, help="target: reference runs (ln f_final / 10)")
+    p.add_argument("--corpus-per-size", type=int, default=64, help="target: corpus runs per lattice size")
+    p.add_argument("--mlp-cache", default=None,
+                   help="target: .npz of the trained network; read when it exists (no corpus, no training), "
+                        "else written after training")
     return p.parse_args()
 
 
@@ -488,12 +498,112 @@ def run_warmstart(args):
     return 0
 
 
+def run_target(args):
+    """The bcc L = 32 four-shell couplings converged to ln f_final, plain against the learned warm start,
+    on the range around the specific-heat peak (workloads.TARGET_L32: E/N in [-2.50, -2.10], bins of
+    1.6 J1, windows of about 216 bins x 2 walkers).  Corpus: converged runs of four-shell couplings at
+    bcc L = 8, 12, 16, 20 (--corpus-per-size each, restricted range [0.6 E_gs, 0], one bin per spin,
+    ln f -> 1e-4), the network trained on them by the library's kernels.  Each target run converges alone
+    on the GPU.  Accuracy: centred rms of ln g against the mean of --target-refs further plain runs
+    converged to ln f_final / 10, and the C(T) peak of every run."""
+    import numpy as np
+    import torch
+    import paper_1411_4212_gb300 as rw
+    from paper_1411_4212_gb300 import warmstart, workloads
+    rank, world, local = dist_init(args.gpus)
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    spec = workloads.TARGET_L32
+    lnf = args.target_lnf
+    t0 = time.perf_counter()
+    if args.mlp_cache and os.path.exists(args.mlp_cache):
+        # a network trained by an earlier run of this leg (same corpus recipe)
+        z = np.load(args.mlp_cache)
+        net = rw.Mlp(warmstart.SHIFT, warmstart.SCALE)
+        net.set_params(z["params"])
+        t, off, hist, meta = z["targets"], z["offsets"], z["loss"], {"converged": bool(z["converged"])}
+        t1 = t2 = time.perf_counter()
+    else:
+        x, t, off, meta = warmstart.corpus(sizes=(8, 12, 16, 20), per_size=args.corpus_per_size, lnf_final=1e-4,
+                                           shells=4, max_samples=2048)
+        t1 = time.perf_counter()
+        net, hist = warmstart.train(x, t, off, steps=4000, lr=2e-3)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if args.mlp_cache:
+            np.savez(args.mlp_cache, params=net.params(), targets=t, offsets=off, loss=hist,
+                     converged=meta["converged"], corpus_s=t1 - t0, training_s=t2 - t1)
+        print(json.dumps({"corpus_runs": int(len(off) - 1), "samples": int(len(t)), "corpus_s": t1 - t0,
+                          "training_s": t2 - t1, "loss_first": float(hist[0]), "loss_last": float(hist[-1])}),
+              file=sys.stderr, flush=True)
+    T = np.linspace(1.2, 2.2, 2001)
+    runs = []
+
+    def one(kind, seed, lnf_final):
+        job = warmstart.target_job(spec, seed=seed, lnf_final=lnf_final)
+        job.init_walkers()
+        pred = None
+        tw = time.perf_counter()        # the warm run's time includes the network's inference
+        if kind == "warm":
+            pred = net.warm_start(job, warmstart.LNF0_WARM)
+        ok, _, moves = warmstart.converge_alone(job)
+        wall = time.perf_counter() - tw
+        lng, cen = job.merge()
+        _, Cv, _ = rw.thermo(lng, cen, job.N, T)
+        rec = {"kind": kind, "seed": seed, "lnf_final": lnf_final, "converged": bool(ok), "wall_s": wall,
+               "moves_per_walker": moves, "T_peak": rw.peak_temperature(T, Cv), "C_max": float(Cv.max()),
+               "windows": job.h, "walkers": job.n_slots, "bins": job.B}
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+        job.close()
+        return rec, lng, pred
+
+    refs = []
+    for r in range(args.target_refs):
+        rec, lng, _ = one("reference", 7000 + r, lnf / 10)
+        runs.append(rec)
+        refs.append(lng)
+    ref = warmstart.reference_curve(refs)
+    for r in range(args.target_replicas):
+        for kind, s0 in (("plain", 8000), ("warm", 9000)):
+            rec, lng, pred = one(kind, s0 + r, lnf)
+            rec["rms_vs_reference"] = warmstart.centred_rms(lng, ref)
+            if pred is not None:
+                rec["prediction_rms_vs_reference"] = warmstart.centred_rms(pred, ref)
+            runs.append(rec)
+    plain = [r for r in runs if r["kind"] == "plain"]
+    warm = [r for r in runs if r["kind"] == "warm"]
+    mean = lambda rs, k: float(np.mean([r[k] for r in rs]))
+    line = {
+        "metric": "time to converged ln g(E), learned warm start / plain REWL (bcc L=32, 4 shells)",
+        "value": mean(warm, "wall_s") / mean(plain, "wall_s"), "unit": "ratio", "higher_is_better": False,
+        "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": f"bcc L=32 J=(1,0.6,-0.05,-0.1), E/N in [-2.50,-2.10], {runs[-1]['bins']} bins "
+                               f"of 1.6 J1, {runs[-1]['windows']} windows x 2 walkers, ln f 1 -> {lnf:g} (plain) or "
+                               f"2^-7 -> {lnf:g} (warm); corpus {len(off) - 1} runs bcc L=8..20, four shells",
+                   "corpus_converged": bool(meta["converged"])},
+        "moves_per_walker": {"plain": mean(plain, "moves_per_walker"), "warm": mean(warm, "moves_per_walker"),
+                             "ratio": mean(warm, "moves_per_walker") / mean(plain, "moves_per_walker")},
+        "wall_s": {"plain": mean(plain, "wall_s"), "warm": mean(warm, "wall_s"), "corpus": t1 - t0,
+                   "training": t2 - t1},
+        "rms_vs_reference": {"plain": mean(plain, "rms_vs_reference"), "warm": mean(warm, "rms_vs_reference")},
+        "T_peak": {k: [r["T_peak"] for r in runs if r["kind"] == k] for k in ("reference", "plain", "warm")},
+        "training": {"samples": int(len(t)), "runs": int(len(off) - 1), "loss_first": float(hist[0]),
+                     "loss_last": float(hist[-1])},
+        "runs": runs,
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
 def run_weak_scaling(args):
     """Trial moves per walker to finish the first Wang-Landau iteration versus lattice size (the
-    paper's weak-scaling measure, Sec. 5, Fig. 3): windows of 64 bins at 75 % overlap, one walker
-    each, their number growing with N (bcc L = 4..12, 5 to 213 windows), against one serial walker
-    over the same range (L <= 8).  Range [0.6 E_gs, 0] with one bin per spin, J = (1, 0.5).  All
-    jobs run in one batch; each leaves the work list when its walkers have halved ln f once."""
+    paper's weak-scaling measure, Sec. 5, Fig. 3, over its L = 10..50 and smaller): windows of 64 bins
+    at 75 % overlap, one walker each, their number growing with N (5 windows at bcc L = 4, 15622 at
+    L = 50, 250 000 spins), against one serial walker over the same range (L <= 8).  Range
+    [0.6 E_gs, 0] with one bin per spin, J = (1, 0.5).  All jobs run in one batch; each leaves the work
+    list when its walkers have halved ln f once."""
     import numpy as np
     import torch
     import paper_1411_4212_gb300 as rw
@@ -503,9 +613,15 @@ def run_weak_scaling(args):
         return 0
     torch.cuda.set_device(local)
     J = (1.0, 0.5)
-    sizes, serial_sizes = (4, 6, 8, 10, 12), (4, 6, 8)
+    sizes = tuple(int(v) for v in args.ws_sizes.split(","))
+    serial_sizes = tuple(L for L in (4, 6, 8) if L <= max(sizes))
+    t0 = time.perf_counter()
     jobs = [warmstart.first_iteration_job(L, J, seed=100 + L) for L in sizes]
     jobs += [warmstart.first_iteration_job(L, J, seed=200 + L, serial=True) for L in serial_sizes]
+    for j in jobs:
+        j.init_walkers()
+    torch.cuda.synchronize()
+    t_init = time.perf_counter() - t0
     t0 = time.perf_counter()
     with rw.Batch(jobs) as b:
         ok, done = b.run_to_convergence(max_intervals=20000, check_every=4)
@@ -515,16 +631,17 @@ def run_weak_scaling(args):
         w = j.walkers()
         rows.append({"L": L, "N": 2 * L ** 3, "windows": j.h, "bins_per_window": j.W,
                      "moves_per_walker": float(w["steps"].mean()), "first_iteration_done": bool(np.all(w["stage"] >= 1)),
-                     "serial": j.h == 1})
+                     "serial": j.h == 1, "lattice_bytes": j.n_slots * 2 * L ** 3 * 8})
         j.close()
     rewl = [r for r in rows if not r["serial"]]
     line = {
         "metric": "trial moves per walker to finish the first WL iteration, largest / smallest lattice",
         "value": rewl[-1]["moves_per_walker"] / rewl[0]["moves_per_walker"], "unit": "ratio",
         "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
-        "config": {"workload": "weak scaling: bcc L=4..12, J=(1,0.5), range [0.6 E_gs, 0], one bin per spin, "
-                               "windows of ~64 bins at 75% overlap (h grows with N), 1 walker per window; "
-                               "serial: one walker over the whole range", "all_done": bool(ok), "wall_s": wall},
+        "config": {"workload": f"weak scaling: bcc L={','.join(map(str, sizes))}, J=(1,0.5), range [0.6 E_gs, 0], "
+                               "one bin per spin, windows of ~64 bins at 75% overlap (h grows with N), 1 walker per "
+                               "window; serial: one walker over the whole range", "all_done": bool(ok),
+                   "init_s": t_init, "wall_s": wall},
         "rows": rows,
     }
     print(json.dumps(line), flush=True)
@@ -541,6 +658,8 @@ def main():
         return run_warmstart(args)
     if args.workload == "weak-scaling":
         return run_weak_scaling(args)
+    if args.workload == "target":
+        return run_target(args)
     import torch
     import paper_1411_4212_gb300 as rw
 
@@ -604,8 +723,9 @@ def main():
 
     # roofline of the walker kernel: lattices in shared memory against the shared-memory bandwidth
     # of this GPU (neighbour spins, ln g and H, records); lattices in global memory against HBM
-    # (the lattice bytes alone: the 8-byte spin codes of the z neighbours and the old spin, the
-    # accepted new spin written back)
+    # (the lattice bytes alone).  Algorithmic bytes per move as the hot path's scope defines them: a
+    # spin is its three FP32 components, 12 B (the library stores it in an 8-byte code, so the
+    # kernel itself moves less than this)
     z = sim.z
     walk_avg_ms = statistics.mean(walk_ms)
     walker_share = sum(walk_ms) / sum(step_ms)
@@ -613,12 +733,12 @@ def main():
     in_smem = "true" if sim.info()["lattice_in_shared"] else "false"
     if in_smem == "true":
         bound = "smem"
-        bytes_per_move = 8 * z + 8 + 2 * 8 + 8 + 4 + 8 * acc_rate
+        bytes_per_move = 12 * z + 12 + 2 * 8 + 8 + 4 + 12 * acc_rate
         peak, _ = rw.measure_smem_bandwidth(stream)
         peak_source = "measured live: conflict-free 16-byte shared-memory loads on every SM"
     else:
         bound = "hbm"
-        bytes_per_move = 8 * z + 8 + 8 * acc_rate
+        bytes_per_move = 12 * z + 12 + 12 * acc_rate
         peak, peak_source = hbm_peak()
     achieved = bytes_per_move * S * workload["exchange_interval"] / (walk_avg_ms * 1e-3)
     nsh = len(workload["J"])

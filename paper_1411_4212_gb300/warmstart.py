@@ -55,13 +55,17 @@ def converge(jobs, max_intervals=400000, check_every=8, autotune=True):
     return ok
 
 
-def corpus(sizes=(4, 5, 6), per_size=64, lnf_final=1e-4, seed0=0):
-    """Converged ln g curves over random couplings: (x [M][6], ln g/N [M], run offsets [R+1], meta)."""
+def corpus(sizes=(4, 5, 6), per_size=64, lnf_final=1e-4, seed0=0, shells=3, max_samples=None):
+    """Converged ln g curves over random couplings: (x [M][6], ln g/N [M], run offsets [R+1], meta).
+    shells = 4 draws a fourth coupling too (workloads.random_couplings4).  max_samples keeps every
+    k-th bin of a run so that it contributes at most that many samples (the curves are smooth on the
+    scale of a few bins)."""
+    draw = workloads.random_couplings4 if shells == 4 else workloads.random_couplings
     jobs, meta = [], []
     k = seed0
     for L in sizes:
         for _ in range(per_size):
-            J = workloads.random_couplings(k)
+            J = draw(k)
             jobs.append(restricted_job(L, J, seed=5000 + k, lnf_final=lnf_final))
             meta.append((L, J))
             k += 1
@@ -70,6 +74,9 @@ def corpus(sizes=(4, 5, 6), per_size=64, lnf_final=1e-4, seed0=0):
     for j in jobs:
         lng, _ = j.merge()
         x, t = mlp_features(j, lng)
+        if max_samples is not None and len(t) > max_samples:
+            step = -(-len(t) // max_samples)
+            x, t = x[::step], t[::step]
         xs.append(x)
         ts.append(t)
         j.close()
@@ -89,7 +96,7 @@ def centred_rms(a, b):
 
 
 def warm_vs_cold(net, L, couplings, lnf_final=1e-5, replicas=2, lnf0=LNF0_WARM, seed0=900, separate=False,
-                 autotune=False):
+                 autotune=False, n_ref=0, lnf_ref=None):
     """For every coupling set: `replicas` cold starts (ln g = 0, ln f0 = 1) and `replicas` warm starts
     (network ln g, ln f0).  Returns (converged, per-set records, wall seconds).  Records hold the moves
     per walker to converge and the centred rms of each converged ln g against the first cold
@@ -97,14 +104,25 @@ def warm_vs_cold(net, L, couplings, lnf_final=1e-5, replicas=2, lnf0=LNF0_WARM, 
     the job's time to converge.  separate=False converges all jobs in one batch (wall = None);
     separate=True converges the cold jobs, then the warm jobs (network inference included), in two
     timed batches: wall = (cold seconds, warm seconds).  autotune=True lets each batch's autotuner
-    pick its launch shape first (its trial moves are ordinary moves of the jobs)."""
+    pick its launch shape first (its trial moves are ordinary moves of the jobs).  n_ref > 0 judges every
+    cold and warm run against an independent reference instead: the mean of n_ref further cold runs
+    converged to lnf_ref (run first, in a batch of their own); cold_rms then has all replicas."""
     import time
-    cold, warm, pred = [], [], []
+    cold, warm, pred, refs = [], [], [], []
     s = seed0
     for J in couplings:
         cold.append([restricted_job(L, J, seed=s + r, lnf_final=lnf_final) for r in range(replicas)])
         warm.append([restricted_job(L, J, seed=s + 100 + r, lnf_final=lnf_final) for r in range(replicas)])
+        refs.append([restricted_job(L, J, seed=s + 200 + r, lnf_final=lnf_ref) for r in range(n_ref)])
         s += 1000
+    ref_curves = []
+    if n_ref > 0:
+        flat_ref = [j for group in refs for j in group]
+        converge(flat_ref, autotune=autotune)
+        for group in refs:
+            ref_curves.append(reference_curve([j.merge()[0] for j in group]))
+            for j in group:
+                j.close()
     for group in cold + warm:
         for j in group:
             j.init_walkers()
@@ -130,13 +148,13 @@ def warm_vs_cold(net, L, couplings, lnf_final=1e-5, replicas=2, lnf0=LNF0_WARM, 
         ok = converge(flat_cold + flat_warm, autotune=autotune)
         wall = None
     out = []
-    for J, cs, ws, p in zip(couplings, cold, warm, pred):
-        ref, _ = cs[0].merge()
+    for i, (J, cs, ws, p) in enumerate(zip(couplings, cold, warm, pred)):
+        ref = ref_curves[i] if n_ref > 0 else cs[0].merge()[0]
         rec = dict(J=J, cold_moves=[], warm_moves=[], cold_rms=[], warm_rms=[],
                    prediction_rms=centred_rms(p, ref))
         for j in cs:
             rec["cold_moves"].append(float(j.walkers()["steps"].mean()))
-        for j in cs[1:]:
+        for j in (cs if n_ref > 0 else cs[1:]):
             rec["cold_rms"].append(centred_rms(j.merge()[0], ref))
         for j in ws:
             rec["warm_moves"].append(float(j.walkers()["steps"].mean()))
@@ -145,6 +163,45 @@ def warm_vs_cold(net, L, couplings, lnf_final=1e-5, replicas=2, lnf0=LNF0_WARM, 
         for j in cs + ws:
             j.close()
     return ok, out, wall
+
+
+def target_job(spec, seed, lnf_final, stream=None):
+    """The bcc L = 32 four-shell run on its range around the specific-heat peak (workloads.TARGET_L32):
+    bins of spec["bin_width"], windows of about spec["window_bins"] bins."""
+    L = spec["L"]
+    N = 2 * L ** 3
+    lo, hi = spec["e_per_spin"]
+    B = int(round((hi - lo) * N / spec["bin_width"]))
+    h = max(2, int(round(1 + (B / spec["window_bins"] - 1) / (1 - spec["overlap"]))))
+    return REWL(kind=BCC, mode=PRODUCTION, L=L, J=spec["J"], e_min=lo * N, e_max=hi * N, n_bins=B, n_windows=h,
+                walkers_per_window=spec["walkers_per_window"], overlap=spec["overlap"], flatness=spec["flatness"],
+                lnf_final=lnf_final, seed=seed, exchange_interval=spec["exchange_interval"], group_size=1,
+                stream=stream)
+
+
+def converge_alone(job, check_every=16, max_intervals=2_000_000):
+    """Converge one (initialised) job on the GPU by itself (a batch of one: graph replays, the job
+    leaves when every walker has ln f < ln f_final); returns (converged, wall seconds, trial moves per
+    walker)."""
+    import time
+    t0 = time.perf_counter()
+    with Batch([job]) as b:
+        ok, _ = b.run_to_convergence(max_intervals=max_intervals, check_every=check_every)
+    wall = time.perf_counter() - t0
+    return ok, wall, float(job.walkers()["steps"].mean())
+
+
+def reference_curve(curves):
+    """Mean of centred ln g curves (an estimate of ln g with the runs' noise averaged down)."""
+    c = np.array([np.asarray(x) - np.mean(x) for x in curves])
+    return c.mean(0)
+
+
+def paired_excess(a, b):
+    """Mean and standard error of a - b over paired samples."""
+    d = np.asarray(a, dtype=float) - np.asarray(b, dtype=float)
+    se = float(d.std(ddof=1) / np.sqrt(len(d))) if len(d) > 1 else float("inf")
+    return float(d.mean()), se
 
 
 def first_iteration_job(L, J, seed, window_bins=64, overlap=0.75, exchange_interval=4000, serial=False):

@@ -28,6 +28,23 @@ def random_couplings(seed):
     return (1.0, float(j2), float(j3))
 
 
+def random_couplings4(seed):
+    """Four shells: J1 = 1, J2 ~ U[0.2, 0.6], J3 ~ U[-0.1, 0.1] as random_couplings, and J4 ~ U[-0.1, 0.1]
+    (the fourth shell of the bcc L = 32 workload's couplings lies inside these ranges)."""
+    g = np.random.Generator(np.random.Philox(key=int(seed)))
+    j2 = g.uniform(0.2, 0.6)
+    j3 = g.uniform(-0.1, 0.1)
+    j4 = g.uniform(-0.1, 0.1)
+    return (1.0, float(j2), float(j3), float(j4))
+
+
+# The bcc L = 32 four-shell couplings on a range around the specific-heat peak: E/N in [-2.50, -2.10]
+# (the peak's energy per spin extrapolates to about -2.31 from oracle runs at L = 4, 5, 6), bins of
+# 1.6 J1 (about the peak temperature), windows of about 216 bins at 75 % overlap, 2 walkers each.
+TARGET_L32 = dict(L=32, J=(1.0, 0.6, -0.05, -0.1), e_per_spin=(-2.50, -2.10), bin_width=1.6, window_bins=216,
+                  walkers_per_window=2, overlap=0.75, flatness=0.8, exchange_interval=4000)
+
+
 def batch64_jobs(jobs_per_size=16, lnf_final=1e-6, exchange_interval=10000):
     """64 independent jobs, 16 per bcc L in {8, 12, 16, 20}: random three-shell couplings (job j keyed by
     seed j), n_bins = N/4 over [E_gs, 0], 8/16/24/32 windows x 4 walkers at 75 % overlap."""
