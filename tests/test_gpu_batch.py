@@ -142,3 +142,36 @@ def test_batch_rejects_mixed_jobs():
         assert info["workers_per_block"] == 2 and info["owner_entries_max"] == 8192
     for h in (a, b, c):
         h.close()
+
+
+def test_batched_convergence_of_mixed_lattices_gives_every_job_its_result():
+    """16 jobs of four lattice sizes (bcc L = 4, 5, 6, 8) with random three-shell couplings, each on its
+    restricted range [0.6 E_gs, 0] with one bin per spin, converged to ln f = 1e-4 in one batch (the
+    batch autotuned first; finished jobs leave the work list).  Every job must reach its ln f target
+    (Sec. 4.2), and its merged ln g (Sec. 4.3) must be finite, mean zero and increasing with E: the
+    range lies below the energy of infinite temperature, so 1/T = d ln g/dE > 0.  Its specific heat
+    (Sec. 4.1, Eq. 3) must peak inside the temperature grid."""
+    from paper_1411_4212_gb300 import warmstart, workloads
+    sizes = (4, 5, 6, 8)
+    jobs = [warmstart.restricted_job(L, workloads.random_couplings(300 + 4 * i + k), seed=40 + 4 * i + k,
+                                     lnf_final=1e-4)
+            for i, L in enumerate(sizes) for k in range(4)]
+    with rw.Batch(jobs) as b:
+        b.autotune(trial_moves=500)
+        converged, n_done = b.run_to_convergence(max_intervals=100000, check_every=8)
+        assert converged and n_done == len(jobs)
+    T = np.linspace(0.8, 5.0, 2101)
+    peaks = []
+    for j in jobs:
+        assert np.all(j.walkers()["lnf"] < 1e-4)
+        lng, cen = j.merge()
+        assert np.all(np.isfinite(lng)) and abs(lng.mean()) < 1e-9 * max(1.0, np.abs(lng).max())
+        k = max(4, j.W // 8)                       # slope over k bins: the bin noise averages out
+        slope = (lng[k:] - lng[:-k]) / (cen[k:] - cen[:-k])
+        assert np.mean(slope > 0) > 0.98, (j.N, np.mean(slope > 0))
+        _, Cv, _ = rw.thermo(lng, cen, j.N, T)
+        tp = rw.peak_temperature(T, Cv)
+        assert T[0] < tp < T[-1], tp
+        peaks.append(tp)
+        j.close()
+    print("T_peak per job:", np.round(peaks, 3))
