@@ -69,9 +69,9 @@ def parse():
                         "bcc L=32 four-shell couplings converged, warm start against plain")
     p.add_argument("--ws-sizes", default="4,6,8,10,16,20,30,40,50",
                    help="weak-scaling: bcc L of the windowed jobs (the paper's Fig. 3 covers L = 10..50)")
-    p.add_argument("--target-lnf", type=float, default=1e-8, help="target: ln f_final of the plain and warm runs")
+    p.add_argument("--target-lnf", type=float, default=1e-6, help="target: ln f_final of the plain and warm runs")
     p.add_argument("--target-replicas", type=int, default=2, help="target: plain and warm runs each")
-    p.add_argument("--target-refs", type=int, default=2, help="target: reference runs (ln f_final / 10)")
+    p.add_argument("--target-refs", type=int, default=1, help="target: reference runs (ln f_final / 10)")
     p.add_argument("--corpus-per-size", type=int, default=64, help="target: corpus runs per lattice size")
     p.add_argument("--mlp-cache", default=None,
                    help="target: .npz of the trained network; read when it exists (no corpus, no training), "
@@ -672,8 +672,8 @@ def main():
     workload, workload_name, _ = WORKLOADS[args.workload]
     sim = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, seed=replica_seed(rank), stream=stream, **workload)
     sim.init_walkers()
-    # lattices in global memory: the conflict-table size is timed before the warm-up (ordinary moves)
-    tune = sim.autotune(trial_moves=2000) if not sim.info()["lattice_in_shared"] else None
+    # the conflict-table size is timed before the warm-up (ordinary moves)
+    tune = sim.autotune(trial_moves=2000)
     S, B = sim.n_slots, sim.B
     moves_per_step = S * workload["exchange_interval"] * I
     out = torch.zeros(B, dtype=torch.float64, device=dev)

@@ -195,17 +195,18 @@ rewl_status rewl_run_stage(rewl_handle* h, rewl_stage_stats* stats);
 rewl_status rewl_walk(rewl_handle* h);
 rewl_status rewl_flatness(rewl_handle* h);
 
-/* Conflict-table autotuner of the pipelined walker with the lattice in global memory (rewl_info
- * .pipelined = 1, .lattice_in_shared = 0).  The paper has no counterpart: the moves it times are
- * those of Sec. 4.2 (Eq. 4); only the launch shape changes.  Times one walker launch of
- * trial_moves (> 0) moves per walker for each table of 8192 down to 512 entries (at most one per
- * site), twice (the second round in reverse order), and keeps the table with the fastest trial.
- * A smaller table leaves more shared memory to L1 and fits more walkers per SM; sites sharing an
- * entry cost extra exact corrections, never a different result.  The default is 2048 entries.
- * Other handles have nothing to tune: their table stays and no move is made.  The timed moves are
- * ordinary Wang-Landau moves: the walkers advance by them (walkers are initialised first if
- * needed).  entries_out, ms_out (host, may be NULL) receive the chosen size and its trial time
- * (0 when nothing was timed).  Blocks until the trials end. */
+/* Conflict-table autotuner of the pipelined walker (rewl_info .pipelined = 1).  The paper has no
+ * counterpart: the moves it times are those of Sec. 4.2 (Eq. 4); only the launch shape changes.  Times
+ * one walker launch of trial_moves (> 0) moves per walker for each table of 8192 down to 512 entries (at
+ * most one per site, and with the lattice in shared memory only tables that fit beside it), twice (the
+ * second round in reverse order), and keeps the table with the fastest trial.  A smaller table leaves
+ * more shared memory to L1 and fits more walkers per SM (a run with more walkers than SMs then needs
+ * fewer waves); sites sharing an entry cost extra exact corrections, never a different result.  The
+ * default is the largest table that fits (lattice in shared memory) or 2048 entries (lattice in global
+ * memory).  Other handles have nothing to tune: their table stays and no move is made.  The timed moves
+ * are ordinary Wang-Landau moves: the walkers advance by them (walkers are initialised first if
+ * needed).  entries_out, ms_out (host, may be NULL) receive the chosen size and its trial time (0 when
+ * nothing was timed).  Blocks until the trials end. */
 rewl_status rewl_autotune(rewl_handle* h, int64_t trial_moves, int32_t* entries_out, double* ms_out);
 
 /* One replica-exchange round between adjacent windows (Sec. 4.3, Eq. 5): round t pairs windows

@@ -822,26 +822,39 @@ rewl_status rewl_autotune(rewl_handle* h, int64_t trial_moves, int32_t* entries_
   if (trial_moves < 1) return fail(h, REWL_EINVAL, "trial_moves must be > 0");
   if (entries_out) *entries_out = h->pipe ? h->own_entries : 0;
   if (ms_out) *ms_out = 0.0;
-  if (!h->pipe || h->pipe_smem_lattice) return REWL_OK;
+  if (!h->pipe) return REWL_OK;
   if (!h->initialized) {
     s = rewl_init_walkers(h);
     if (s != REWL_OK) return s;
   }
   int own_full = 256;
   while (own_full < h->N && own_full < 8192) own_full *= 2;
+  int dev = 0, max_smem = 0;
+  CUDA_TRY(h, cudaGetDevice(&dev));
+  CUDA_TRY(h, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CUDA_TRY(h, cudaEventCreate(&e0));
   cudaError_t e = cudaEventCreate(&e1);
   const int e_prev = h->own_entries;
-  // two rounds, the second in reverse order; each candidate keeps its faster trial
+  // two rounds, the second in reverse order; each candidate keeps its faster trial.  With the lattice
+  // in shared memory only tables that fit beside it are candidates; a smaller one can fit a second
+  // walker per SM.
   std::vector<int> cands;
-  for (int c = own_full; c >= 512; c /= 2) cands.push_back(c);
+  for (int c = own_full; c >= 512; c /= 2)
+    if (walker_pipe_smem_bytes(h->traj, h->pipe_smem_lattice, h->N, h->W, c) + 1024 <= (size_t)max_smem)
+      cands.push_back(c);
+  if (cands.size() < 2) {   // nothing to choose between: no trial, no move
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(h, REWL_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    return REWL_OK;
+  }
   std::vector<double> t_min(cands.size(), -1.0);
   for (int round = 0; round < 2 && e == cudaSuccess; ++round) {
     for (size_t k = 0; k < cands.size() && e == cudaSuccess; ++k) {
       const size_t c = round == 0 ? k : cands.size() - 1 - k;
       h->own_entries = cands[c];
-      h->pipe_smem_bytes = walker_pipe_smem_bytes(h->traj, false, h->N, h->W, cands[c]);
+      h->pipe_smem_bytes = walker_pipe_smem_bytes(h->traj, h->pipe_smem_lattice, h->N, h->W, cands[c]);
       const WalkerArgs a = walker_args(h, false, false, trial_moves);
       e = cudaEventRecord(e0, h->stream);
       if (e == cudaSuccess) e = launch_walk(h, a);
@@ -862,7 +875,7 @@ rewl_status rewl_autotune(rewl_handle* h, int64_t trial_moves, int32_t* entries_
   cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   h->own_entries = e == cudaSuccess ? best_e : e_prev;
-  h->pipe_smem_bytes = walker_pipe_smem_bytes(h->traj, false, h->N, h->W, h->own_entries);
+  h->pipe_smem_bytes = walker_pipe_smem_bytes(h->traj, h->pipe_smem_lattice, h->N, h->W, h->own_entries);
   if (e != cudaSuccess) return fail(h, REWL_ECUDA, std::string("autotune trial: ") + cudaGetErrorString(e));
   int32_t err = 0;
   CUDA_TRY(h, cudaMemcpyAsync(&err, h->d_ctrl, sizeof err, cudaMemcpyDeviceToHost, h->stream));

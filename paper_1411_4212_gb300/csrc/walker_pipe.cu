@@ -148,41 +148,6 @@ __device__ __forceinline__ void field_one_lane(const Lat& lat, int X, int Y, int
   }
 }
 
-// Warm the L2 with the spin codes a move at half-unit coordinates (X, Y, Z) will read: the site and its
-// neighbours over NSH shells (every index lies in [0, N)).  A prefetch only moves data towards the
-// SM; the later loads still read whatever the lattice then holds.
-template <int NSH>
-__device__ __forceinline__ void prefetch_neighbourhood(const float2* codes, int X, int Y, int Z, int L) {
-  constexpr ShellTable T = make_shells(NSH);
-  const int twoL = 2 * L, LL = L * L;
-  int xw[7], yw[7], zw[7];
-#pragma unroll
-  for (int d = -3; d <= 3; ++d) {
-    int x = X + d, y = Y + d, z = Z + d;
-    x += (x < 0) ? twoL : 0;
-    x -= (x >= twoL) ? twoL : 0;
-    y += (y < 0) ? twoL : 0;
-    y -= (y >= twoL) ? twoL : 0;
-    z += (z < 0) ? twoL : 0;
-    z -= (z >= twoL) ? twoL : 0;
-    xw[d + 3] = x;
-    yw[d + 3] = L * y;
-    zw[d + 3] = LL * z;
-  }
-  const int s = X & 1;
-  const int par_same = s * (L + LL), par_flip = (s ^ 1) * (L + LL);
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(codes + (xw[3] + yw[3] + zw[3] - par_same)));
-#pragma unroll
-  for (int j = 0; j < T.z; ++j) {
-    const int n = xw[T.dx[j] + 3] + yw[T.dy[j] + 3] + zw[T.dz[j] + 3] - ((T.dx[j] & 1) ? par_flip : par_same);
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(codes + n));
-  }
-}
-
-// The code array of a production global lattice (null for the other lattice types, never prefetched).
-__device__ __forceinline__ const float2* glat_codes(const SpinCodes& l) { return l.c; }
-__device__ __forceinline__ const float2* glat_codes(const SpinPlanes<double>&) { return nullptr; }
-
 // Uniform in [1, 2) from the top 23 bits of a word (no integer-to-float conversion).
 __device__ __forceinline__ float one_to_two(uint32_t x) { return __uint_as_float(0x3f800000u | (x >> 9)); }
 
@@ -267,29 +232,11 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
     for (int s2 = 0; s2 < 4; ++s2) Jsh[s2] = kTraj ? (Real)a.geo.Jsh_d[s2] : (Real)a.geo.Jsh_f[s2];
     int site_prev = 0;
     bool valid_prev = false;
-    // production, lattice in global memory: each batch's Philox block is drawn one batch ahead, and the
-    // next batch's neighbourhoods are prefetched into the L2 while this batch gathers its own (the walk
-    // is bound by gather misses in flight per SM; misses that hit the L2 are served several times faster)
-    constexpr bool kAhead = !kTraj && !kSmem;
-    uint4 x_next = make_uint4(0u, 0u, 0u, 0u);
-    if constexpr (kAhead)
-      x_next = philox10(make_uint4((uint32_t)(t0 + lane), (uint32_t)((unsigned long long)(t0 + lane) >> 32), 0u, 0u),
-                        key);
     for (int b = 0; b < nb; ++b) {
       if (b >= 2) named_sync(kBarDone + (b & 1));
       const int cur = b & 1;
       const bool valid = (long long)b * 32 + lane < moves;
       const unsigned long long t = (unsigned long long)(t0 + (long long)b * 32 + lane);
-      uint4 x_this = x_next;
-      if constexpr (kAhead) {
-        const unsigned long long tn = t + 32ull;
-        x_next = philox10(make_uint4((uint32_t)tn, (uint32_t)(tn >> 32), 0u, 0u), key);
-        if ((long long)(b + 1) * 32 + lane < moves) {
-          int Xn, Yn, Zn;
-          bcc_coords((int)__umulhi(x_next.x, (uint32_t)N), L, a.geo.divL, Xn, Yn, Zn);
-          prefetch_neighbourhood<NSH>(glat_codes(glat), Xn, Yn, Zn, L);
-        }
-      }
       int site;
       Real nx, ny, nz;
       double u = 0.0;
@@ -302,7 +249,7 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         ny = (Real)dny;
         nz = (Real)dnz;
       } else {
-        const uint4 x = kAhead ? x_this : philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0u, 0u), key);
+        const uint4 x = philox10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0u, 0u), key);
         site = (int)__umulhi(x.x, (uint32_t)N);
         const float uf = (one_to_two(x.y) - 1.0f) + 0x1.0p-24f;                // (0, 1)
         lu = __float2int_rn(__logf(uf) * 1048576.0f);

@@ -179,13 +179,15 @@ def target_job(spec, seed, lnf_final, stream=None):
                 stream=stream)
 
 
-def converge_alone(job, check_every=16, max_intervals=2_000_000):
+def converge_alone(job, check_every=16, max_intervals=2_000_000, autotune=True):
     """Converge one (initialised) job on the GPU by itself (a batch of one: graph replays, the job
-    leaves when every walker has ln f < ln f_final); returns (converged, wall seconds, trial moves per
-    walker)."""
+    leaves when every walker has ln f < ln f_final), its launch shape autotuned first (ordinary moves,
+    counted); returns (converged, wall seconds, trial moves per walker)."""
     import time
     t0 = time.perf_counter()
     with Batch([job]) as b:
+        if autotune:
+            b.autotune(trial_moves=2000)
         ok, _ = b.run_to_convergence(max_intervals=max_intervals, check_every=check_every)
     wall = time.perf_counter() - t0
     return ok, wall, float(job.walkers()["steps"].mean())

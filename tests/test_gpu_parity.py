@@ -129,7 +129,26 @@ def test_global_memory_lattice_autotune_moves_are_ordinary_moves():
     gpu.close()
 
 
-def test_autotune_leaves_shared_lattice_walkers_alone():
+def test_shared_lattice_autotune_moves_are_ordinary_moves():
+    """With the lattice in shared memory the autotuner times the tables that fit beside it (1024 and 512
+    entries at bcc L = 8, twice each): ordinary moves again, bit for bit with the oracle."""
+    gpu, orc = make_pair(group_size=1, L=8, J=(1.0, 0.5), n_bins=600, n_windows=3, walkers_per_window=2,
+                         overlap=0.75, flatness=0.8, lnf_final=1e-8, seed=5, exchange_interval=1500)
+    assert gpu.info()["lattice_in_shared"] == 1 and gpu.info()["conflict_entries"] == 1024
+    gpu.init_walkers()
+    orc.init_walkers()
+    t = gpu.autotune(trial_moves=300)
+    assert t["conflict_entries"] in (512, 1024) and t["trial_ms"] > 0
+    orc.run_moves_only(4 * 300)
+    assert_same_state(gpu, orc)
+    gpu.run_intervals(2)
+    orc.run_intervals(2)
+    assert_same_state(gpu, orc)
+    gpu.close()
+
+
+def test_autotune_leaves_single_table_walkers_alone():
+    """bcc L = 4 (128 sites) has one table size to offer: no trial, no move."""
     gpu, _ = make_pair(group_size=1, exchange_interval=1000, **CFG1)
     gpu.init_walkers()
     steps = gpu.walkers()["steps"].copy()
