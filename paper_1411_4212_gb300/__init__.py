@@ -354,16 +354,42 @@ class REWL:
         assert lng.size == self.B
         _check(self._lib.rewl_set_initial_lng(self._h, _ptr(lng), float(lnf0)), self._h)
 
-    def run_to_convergence(self, max_stages=1000):
+    def run_to_convergence(self, max_stages=1000, log=None):
         """Stages (rewl_run_stage) until every walker has ln f < lnf_final.  Stops at the first stage
-        that a cap (max_moves_per_stage, timeout_s) ended: that stage's dict has capped = True."""
+        that a cap (max_moves_per_stage, timeout_s) ended: that stage's dict has capped = True.
+        log: a writable text file that receives one JSON line per stage (stage_report of the stage)."""
+        import json
         stages = []
         for _ in range(max_stages):
             st = self.run_stage()
             stages.append(st)
+            if log is not None:
+                log.write(json.dumps(self.stage_report(st)) + "\n")
+                log.flush()
             if st["all_done"] or st["capped"]:
                 break
         return stages
+
+    def stage_report(self, stage=None):
+        """The run's state as plain numbers (the quantities the paper reports, Sec. 5): moves/s of the stage
+        when its stats are given, accept rate, replica-exchange acceptance per window pair, round trips
+        per configuration, ln f per walker and each walker's flatness ratio min H / mean H."""
+        w = self.walkers()
+        att, acc = self.exchange_counts()
+        trips, _ = self.round_trips()
+        c = self.counters()
+        H = w["H"].astype(np.float64)
+        mean = H.mean(axis=1)
+        rep = {"moves": int(c["moves"]), "accept_rate": c["accepts"] / max(1, c["moves"]),
+               "exchange_acceptance": [float(a) / max(1, int(t)) for a, t in zip(acc, att)],
+               "round_trips": [int(v) for v in trips], "lnf": [float(v) for v in w["lnf"]],
+               "stage": [int(v) for v in w["stage"]],
+               "flatness_ratio": [float(m) for m in np.where(mean > 0, H.min(axis=1) / np.maximum(mean, 1e-300), 0.0)]}
+        if stage is not None:
+            rep["stage_moves_per_s"] = stage["moves"] / max(stage["elapsed_ms"] * 1e-3, 1e-12)
+            rep["stage_intervals"] = stage["intervals"]
+            rep["capped"] = bool(stage.get("capped", False))
+        return rep
 
     # -- state -----------------------------------------------------------------------------
     def info(self):

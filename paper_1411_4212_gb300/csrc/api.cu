@@ -724,6 +724,7 @@ rewl_status rewl_create_partition(const rewl_lattice* lat, const rewl_couplings*
 }
 
 rewl_status rewl_init_walkers(rewl_handle* h) {
+  NvtxRange nvtx_("rewl_init_walkers");
   rewl_status s = check_ready(h);
   if (s != REWL_OK) return s;
   const WalkerArgs a = walker_args(h, true, false, 0);
@@ -803,6 +804,7 @@ int rewl::job_bins(const rewl_handle* h) { return h->B; }
 extern "C" {
 
 rewl_status rewl_walk(rewl_handle* h) {
+  NvtxRange nvtx_("rewl_walk");
   rewl_status s = check_ready(h);
   if (s != REWL_OK) return s;
   if (!h->initialized) {
@@ -817,6 +819,7 @@ rewl_status rewl_walk(rewl_handle* h) {
 }
 
 rewl_status rewl_autotune(rewl_handle* h, int64_t trial_moves, int32_t* entries_out, double* ms_out) {
+  NvtxRange nvtx_("rewl_autotune");
   rewl_status s = check_ready(h);
   if (s != REWL_OK) return s;
   if (trial_moves < 1) return fail(h, REWL_EINVAL, "trial_moves must be > 0");
@@ -887,6 +890,7 @@ rewl_status rewl_autotune(rewl_handle* h, int64_t trial_moves, int32_t* entries_
 }
 
 rewl_status rewl_flatness(rewl_handle* h) {
+  NvtxRange nvtx_("rewl_flatness");
   rewl_status s = check_ready(h);
   if (s != REWL_OK) return s;
   CUDA_TRY(h, launch_flatness(flatness_args(h), h->S, h->stream));
@@ -977,6 +981,7 @@ static rewl_status read_stage(rewl_handle* h, std::vector<int32_t>& stage, std::
 }
 
 rewl_status rewl_run_intervals(rewl_handle* h, int n, rewl_stage_stats* stats) {
+  NvtxRange nvtx_("rewl_run_intervals");
   rewl_status s = check_whole(h);
   if (s != REWL_OK) return s;
   if (n < 0) return fail(h, REWL_EINVAL, "n_intervals must be >= 0");
@@ -1005,6 +1010,7 @@ rewl_status rewl_run_intervals(rewl_handle* h, int n, rewl_stage_stats* stats) {
 }
 
 rewl_status rewl_run_stage(rewl_handle* h, rewl_stage_stats* stats) {
+  NvtxRange nvtx_("rewl_run_stage");
   rewl_status s = check_whole(h);
   if (s != REWL_OK) return s;
   if (!h->initialized) {
@@ -1050,6 +1056,7 @@ rewl_status rewl_run_stage(rewl_handle* h, rewl_stage_stats* stats) {
 }
 
 rewl_status rewl_exchange(rewl_handle* h, rewl_stage_stats* stats) {
+  NvtxRange nvtx_("rewl_exchange");
   rewl_status s = check_whole(h);
   if (s != REWL_OK) return s;
   if (!h->initialized) {
@@ -1083,6 +1090,7 @@ static MergeArgs merge_args(rewl_handle* h, double* out) {
 }
 
 rewl_status rewl_merge_lng_device(rewl_handle* h, double* out) {
+  NvtxRange nvtx_("rewl_merge_lng_device");
   rewl_status s = check_whole(h);
   if (s != REWL_OK) return s;
   if (!out) return fail(h, REWL_EINVAL, "lng_out_dev is NULL");
@@ -1091,6 +1099,7 @@ rewl_status rewl_merge_lng_device(rewl_handle* h, double* out) {
 }
 
 rewl_status rewl_merge_lng(rewl_handle* h, double* lng_out, double* centres) {
+  NvtxRange nvtx_("rewl_merge_lng");
   rewl_status s = check_whole(h);
   if (s != REWL_OK) return s;
   if (!lng_out) return fail(h, REWL_EINVAL, "lng_out is NULL");
@@ -1430,6 +1439,7 @@ rewl_status rewl_partition_slots(rewl_handle* h, int32_t* gid) {
 }
 
 rewl_status rewl_partition_bins(rewl_handle* h, int32_t* bins) {
+  NvtxRange nvtx_("rewl_partition_bins");
   rewl_status s = check_part(h);
   if (s != REWL_OK) return s;
   if (!bins) return fail(h, REWL_EINVAL, "bins is NULL");
@@ -1442,6 +1452,7 @@ rewl_status rewl_partition_bins(rewl_handle* h, int32_t* bins) {
 }
 
 rewl_status rewl_partition_lookups(rewl_handle* h, const int32_t* bins_all, int64_t* lk) {
+  NvtxRange nvtx_("rewl_partition_lookups");
   rewl_status s = check_part(h);
   if (s != REWL_OK) return s;
   if (!bins_all || !lk) return fail(h, REWL_EINVAL, "NULL argument");
@@ -1460,6 +1471,7 @@ rewl_status rewl_partition_lookups(rewl_handle* h, const int32_t* bins_all, int6
 }
 
 rewl_status rewl_partition_exchange(rewl_handle* h, const int32_t* bins_all, const int64_t* lk_all, int32_t* swap_with) {
+  NvtxRange nvtx_("rewl_partition_exchange");
   rewl_status s = check_part(h);
   if (s != REWL_OK) return s;
   if (!bins_all || !lk_all || !swap_with) return fail(h, REWL_EINVAL, "NULL argument");
@@ -1489,6 +1501,7 @@ rewl_status rewl_slot_state_bytes(rewl_handle* h, int64_t* bytes) {
 }
 
 rewl_status rewl_slot_export(rewl_handle* h, int32_t g, void* buf) {
+  NvtxRange nvtx_("rewl_slot_export");
   rewl_status s = check_part(h);
   if (s != REWL_OK) return s;
   if (!buf || g < 0 || g >= h->S_global || h->pos_host[g] < 0) return fail(h, REWL_EINVAL, "slot not hosted here or NULL buffer");
@@ -1536,6 +1549,7 @@ rewl_status rewl_slot_export(rewl_handle* h, int32_t g, void* buf) {
 }
 
 rewl_status rewl_slot_import(rewl_handle* h, int32_t g_out, const void* buf) {
+  NvtxRange nvtx_("rewl_slot_import");
   rewl_status s = check_part(h);
   if (s != REWL_OK) return s;
   if (!buf || g_out < 0 || g_out >= h->S_global || h->pos_host[g_out] < 0)
@@ -1675,6 +1689,7 @@ rewl_status rewl_state_bytes(rewl_handle* h, int64_t* bytes) {
 }
 
 rewl_status rewl_save_state(rewl_handle* h, void* buf, int64_t bytes) {
+  NvtxRange nvtx_("rewl_save_state");
   rewl_status s = check_ready(h);
   if (s != REWL_OK) return s;
   const size_t n = state_bytes(h);
@@ -1698,6 +1713,7 @@ rewl_status rewl_save_state(rewl_handle* h, void* buf, int64_t bytes) {
 }
 
 rewl_status rewl_load_state(rewl_handle* h, const void* buf, int64_t bytes) {
+  NvtxRange nvtx_("rewl_load_state");
   rewl_status s = check_ready(h);
   if (s != REWL_OK) return s;
   const size_t n = state_bytes(h);

@@ -382,6 +382,7 @@ extern "C" rewl_status rewl_batch_set_tuning(rewl_batch* b, const rewl_batch_tun
 
 extern "C" rewl_status rewl_batch_autotune(rewl_batch* b, int64_t trial_moves, rewl_batch_tuning* chosen,
                                            double* ms_out) {
+  NvtxRange nvtx_("rewl_batch_autotune");
   rewl_status s = check_batch(b);
   if (s != REWL_OK) return s;
   if (trial_moves < 1) return bfail(b, REWL_EINVAL, "trial_moves must be > 0");
@@ -454,6 +455,7 @@ extern "C" rewl_status rewl_batch_autotune(rewl_batch* b, int64_t trial_moves, r
 }
 
 extern "C" rewl_status rewl_batch_run_intervals(rewl_batch* b, int n_intervals) {
+  NvtxRange nvtx_("rewl_batch_run_intervals");
   rewl_status s = check_batch(b);
   if (s != REWL_OK) return s;
   if (n_intervals < 0) return bfail(b, REWL_EINVAL, "n_intervals must be >= 0");
@@ -462,6 +464,7 @@ extern "C" rewl_status rewl_batch_run_intervals(rewl_batch* b, int n_intervals) 
 
 extern "C" rewl_status rewl_batch_run_to_convergence(rewl_batch* b, int64_t max_intervals, int check_every,
                                                      int* n_done) {
+  NvtxRange nvtx_("rewl_batch_run_to_convergence");
   rewl_status s = check_batch(b);
   if (s != REWL_OK) return s;
   if (max_intervals < 1 || check_every < 1) return bfail(b, REWL_EINVAL, "max_intervals and check_every must be >= 1");

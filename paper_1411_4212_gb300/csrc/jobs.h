@@ -3,10 +3,20 @@
 
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rewl.h"
 #include "walker.h"
 
 namespace rewl {
+
+// NVTX range over one C-ABI call (host timeline of a profiler; nothing happens without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct JobView {
   int kind, N, z, L, S, W, h, m, n_shells;

@@ -3,6 +3,8 @@ iteration per call (rewl_run_stage, Sec. 4.2) and its caps, the standalone repli
 (rewl_exchange, Sec. 4.3, Eq. 5), the three split launches of an interval (rewl_walk, rewl_exchange,
 rewl_flatness), and the temperature of the specific-heat peak (rewl_peak_temperature, Sec. 4.1, Eq. 3)."""
 import ctypes as C
+import io
+import json
 
 import numpy as np
 import pytest
@@ -130,3 +132,22 @@ def test_peak_temperature_matches_oracle():
         t = T[: c.size] if c.size > 1 else np.array([2.0])
         assert rw.peak_temperature(t, c) == oracle.peak(t, c)
     gpu.close()
+
+
+def test_stage_log_reports_the_run():
+    """run_to_convergence(log=...) writes one JSON line per stage: moves/s, accept rate, exchange
+    acceptance per window pair, round trips, ln f, stage and flatness ratio per walker."""
+    g = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, group_size=1, **CONVERGING)
+    buf = io.StringIO()
+    stages = g.run_to_convergence(max_stages=40, log=buf)
+    lines = [json.loads(x) for x in buf.getvalue().splitlines()]
+    assert len(lines) == len(stages) and stages[-1]["all_done"]
+    last = lines[-1]
+    assert last["stage_moves_per_s"] > 0 and 0 < last["accept_rate"] < 1
+    assert len(last["exchange_acceptance"]) == g.h - 1 and all(0 <= a <= 1 for a in last["exchange_acceptance"])
+    assert len(last["lnf"]) == g.n_slots and max(last["lnf"]) < CONVERGING["lnf_final"]
+    for a, b in zip(lines, lines[1:]):      # every stage halves ln f of each walker still active at its start
+        assert all(sb >= sa for sa, sb in zip(a["stage"], b["stage"]))
+        assert all(sb > sa for sa, sb, f in zip(a["stage"], b["stage"], a["lnf"]) if f >= CONVERGING["lnf_final"])
+    assert lines[-1]["stage"] == [int(v) for v in g.walkers()["stage"]]
+    g.close()
