@@ -148,120 +148,6 @@ __device__ __forceinline__ void field_one_lane(const Lat& lat, int X, int Y, int
   }
 }
 
-// The z neighbours of a bcc site, grouped by cubic cell.  Site 2c + b is sublattice b of cell c, so the
-// two sites of a cell are one 16-byte pair of production codes.  For a site of sublattice s, half-unit
-// offset o (all three components of one parity) lands in cell offset (s + o) >> 1 (floor, per
-// component) at sublattice (s + o) & 1.  The 50 neighbours over four shells and the site itself fill 35
-// cells for either s.  sh[c][b] is the shell of the neighbour at sublattice b of cell c (0..3), 4 for the
-// site itself, -1 when that site is not read.
-struct CellTable {
-  int cx[kMaxSlotsPerSite], cy[kMaxSlotsPerSite], cz[kMaxSlotsPerSite], sh[kMaxSlotsPerSite][2];
-  int n;
-};
-
-constexpr CellTable make_cells(int nsh, int s) {
-  const ShellTable T = make_shells(nsh);
-  CellTable c{};
-  c.n = 0;
-  for (int j = -1; j < T.z; ++j) {
-    const int ox = j < 0 ? 0 : T.dx[j], oy = j < 0 ? 0 : T.dy[j], oz = j < 0 ? 0 : T.dz[j];
-    const int x = (s + ox) >> 1, y = (s + oy) >> 1, z = (s + oz) >> 1, b = (s + ox) & 1;
-    int k = 0;
-    while (k < c.n && !(c.cx[k] == x && c.cy[k] == y && c.cz[k] == z)) ++k;
-    if (k == c.n) {
-      c.cx[k] = x;
-      c.cy[k] = y;
-      c.cz[k] = z;
-      c.sh[k][0] = -1;
-      c.sh[k][1] = -1;
-      ++c.n;
-    }
-    c.sh[k][b] = j < 0 ? 4 : T.sh[j];
-  }
-  return c;
-}
-
-// Production walker over a lattice of codes in global memory: the local field of site `site` (half-unit
-// coordinates X, Y, Z), summed per shell and multiplied by each shell's coupling once, and the site's
-// own spin.  Loads whole cells (one 16-byte load for both codes of a cell) in the cell order of
-// make_cells; the cell list of the site's sublattice is selected per lane without branches.  The
-// owner-table words of the neighbour sites are OR-ed into own0 / own1.
-template <int NSH>
-__device__ __forceinline__ void field_cells(const float2* __restrict__ codes, int X, int Y, int Z, int L,
-                                            const float (&Jsh)[4], float& hx, float& hy, float& hz, float& ox,
-                                            float& oy, float& oz, const uint2* own, uint32_t omask, uint32_t& own0,
-                                            uint32_t& own1) {
-  constexpr CellTable C0 = make_cells(NSH, 0), C1 = make_cells(NSH, 1);
-  static_assert(C0.n == C1.n, "both sublattices read the same number of cells");
-  const int s = X & 1;
-  const int x = X >> 1, y = Y >> 1, z = Z >> 1;
-  int xw[5], yw[5], zw[5];
-#pragma unroll
-  for (int d = -2; d <= 2; ++d) {
-    int a = x + d, b = y + d, c = z + d;
-    a += a < 0 ? L : 0;
-    a -= a >= L ? L : 0;
-    b += b < 0 ? L : 0;
-    b -= b >= L ? L : 0;
-    c += c < 0 ? L : 0;
-    c -= c >= L ? L : 0;
-    xw[d + 2] = a;
-    yw[d + 2] = L * b;
-    zw[d + 2] = L * L * c;
-  }
-  const float4* q4 = reinterpret_cast<const float4*>(codes);
-  float tx[4] = {0.f, 0.f, 0.f, 0.f}, ty[4] = {0.f, 0.f, 0.f, 0.f}, tz[4] = {0.f, 0.f, 0.f, 0.f};
-  ox = oy = oz = 0.f;
-#pragma unroll
-  for (int c = 0; c < C0.n; ++c) {
-    const int ci0 = xw[C0.cx[c] + 2] + yw[C0.cy[c] + 2] + zw[C0.cz[c] + 2];
-    const int ci1 = xw[C1.cx[c] + 2] + yw[C1.cy[c] + 2] + zw[C1.cz[c] + 2];
-    const int ci = s ? ci1 : ci0;
-    const float4 q = q4[ci];
-    float v[2][3];
-    oct_decode(make_float2(q.x, q.y), v[0][0], v[0][1], v[0][2]);
-    oct_decode(make_float2(q.z, q.w), v[1][0], v[1][1], v[1][2]);
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int k0 = C0.sh[c][b], k1 = C1.sh[c][b];
-      if (k0 < 0 && k1 < 0) continue;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (k >= NSH || (k0 != k && k1 != k)) continue;
-        // this site adds to shell k for one sublattice, or for both
-        const bool use = (k0 == k && k1 == k) ? true : (k1 == k ? s != 0 : s == 0);
-        tx[k] += use ? v[b][0] : 0.f;
-        ty[k] += use ? v[b][1] : 0.f;
-        tz[k] += use ? v[b][2] : 0.f;
-      }
-      if (k0 == 4 || k1 == 4) {
-        const bool self = (k0 == 4 && k1 == 4) ? true : (k1 == 4 ? s != 0 : s == 0);
-        ox = self ? v[b][0] : ox;
-        oy = self ? v[b][1] : oy;
-        oz = self ? v[b][2] : oz;
-      }
-      const bool nb0 = k0 >= 0 && k0 < 4, nb1 = k1 >= 0 && k1 < 4;
-      if (nb0 || nb1) {
-        const bool nb = (nb0 && nb1) ? true : (nb1 ? s != 0 : s == 0);
-        if (nb) {
-          const uint2 o = own[(2 * ci + b) & omask];
-          own0 |= o.x;
-          own1 |= o.y;
-        }
-      }
-    }
-  }
-  hx = 0.f;
-  hy = 0.f;
-  hz = 0.f;
-#pragma unroll
-  for (int k = 0; k < NSH; ++k) {
-    hx = fmaf(Jsh[k], tx[k], hx);
-    hy = fmaf(Jsh[k], ty[k], hy);
-    hz = fmaf(Jsh[k], tz[k], hz);
-  }
-}
-
 // Uniform in [1, 2) from the top 23 bits of a word (no integer-to-float conversion).
 __device__ __forceinline__ float one_to_two(uint32_t x) { return __uint_as_float(0x3f800000u | (x >> 9)); }
 
@@ -386,18 +272,14 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       if (valid) atomicOr(own32 + 2 * (site & omask) + cur, 1u << lane);
       __syncwarp();
       uint32_t o0 = 0, o1 = 0;
-      Real hx, hy, hz, ox, oy, oz;
-      if constexpr (!kTraj && !kSmem) {
-        // codes in global memory: whole cells, one load per cell (35 loads for 51 sites at 4 shells)
-        field_cells<NSH>(glat.c, X, Y, Z, L, Jsh, hx, hy, hz, ox, oy, oz, own, omask, o0, o1);
-      } else {
-        field_one_lane<kTraj, NSH>(lat, X, Y, Z, L, Jsh, hx, hy, hz, own, omask, o0, o1);
-        lat.get(site, ox, oy, oz);
-      }
+      Real hx, hy, hz;
+      field_one_lane<kTraj, NSH>(lat, X, Y, Z, L, Jsh, hx, hy, hz, own, omask, o0, o1);
       const uint2 oself = own[site & omask];
       o0 |= oself.x;
       o1 |= oself.y;
       const uint32_t ocur = cur ? o1 : o0, oprev = cur ? o0 : o1;
+      Real ox, oy, oz;
+      lat.get(site, ox, oy, oz);
       Rec<kTraj>& r = rec[cur * 32 + lane];
       if constexpr (kTraj) {
         const double dx = __dsub_rn(nx, ox), dy = __dsub_rn(ny, oy), dz = __dsub_rn(nz, oz);
