@@ -579,6 +579,10 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
     //                 (low-energy windows);
     //   sequential -- one move at a time: many full resolutions (bins as narrow as the temperature).
     enum { kScan = 0, kBlocks = 1, kSequential = 2 };
+    // several sites share an owner entry (lattices in global memory; a shared-memory lattice keeps
+    // its walker's code as it is, which measured faster at bcc L = 16 where its table has an entry
+    // per site)
+    const bool aliased = !kSmem && (long long)omask + 1 < (long long)N;
     const int forced = a.resolver - 1;      // -1: per-batch choice
     int path = forced >= 0 ? forced : kBlocks;
     int n_scan = 0, n_blocks = 0, n_seq = 0;   // batches per path
@@ -594,8 +598,30 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       // ---- parallel part: lane = move index ----
       Rec<false>& mine = Rc[lane];
       {
+        // An owner table smaller than the lattice is hashed, so a conflict bit may name a move whose
+        // site is neither this move's site nor one of its neighbours: such a move cannot change this
+        // move's field or old spin.  Drop those bits once here -- from batch b-1 (accepted moves)
+        // and from this batch (before any is resolved) -- so that only real conflicts become events
+        // below.  (At bcc L = 32 with 2048 entries, 92 % of the flagged moves were such aliases.)
+        uint32_t m = lane < nvalid ? (mine.cprev & acc_prev) : 0u;
+        const uint32_t cc = (lane < nvalid && aliased) ? mine.ccur : 0u;
+        if (aliased && (m | cc)) {
+          const int p0 = mine.site;
+          uint32_t real_prev = 0u, real_cur = 0u;
+          for (uint32_t t = m; t; t &= t - 1u) {
+            const int j = __ffs(t) - 1;
+            const int q = Rp[j].site;
+            if (q == p0 || coupling(p0, q) != 0.0f) real_prev |= 1u << j;
+          }
+          for (uint32_t t = cc; t; t &= t - 1u) {
+            const int j = __ffs(t) - 1;
+            const int q = Rc[j].site;
+            if (q == p0 || coupling(p0, q) != 0.0f) real_cur |= 1u << j;
+          }
+          m = real_prev;
+          if (real_cur != cc) pk[cur * 32 + lane].z = (int)real_cur;
+        }
         // accepted moves of batch b-1 around this move: correct h and o, then dE
-        const uint32_t m = lane < nvalid ? (mine.cprev & acc_prev) : 0u;
         if (m) {
           float hx = mine.hx, hy = mine.hy, hz = mine.hz, ox = mine.ox, oy = mine.oy, oz = mine.oz;
           correct(Rp, m, mine.site, hx, hy, hz, ox, oy, oz);
