@@ -233,7 +233,6 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
     int site_prev = 0;
     bool valid_prev = false;
     for (int b = 0; b < nb; ++b) {
-      if (b >= 2) named_sync(kBarDone + (b & 1));
       const int cur = b & 1;
       const bool valid = (long long)b * 32 + lane < moves;
       const unsigned long long t = (unsigned long long)(t0 + (long long)b * 32 + lane);
@@ -273,6 +272,9 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
       __syncwarp();
       uint32_t o0 = 0, o1 = 0;
       Real hx, hy, hz;
+      // the draws and the owner-table insert above do not touch the lattice, so they overlap the
+      // resolver's publication of batch b-2; the lattice holds every batch up to b-2 after DONE
+      if (b >= 2) named_sync(kBarDone + (b & 1));
       field_one_lane<kTraj, NSH>(lat, X, Y, Z, L, Jsh, hx, hy, hz, own, omask, o0, o1);
       const uint2 oself = own[site & omask];
       o0 |= oself.x;

@@ -224,6 +224,7 @@ def test_initial_drive_cap_reports_timeout():
 
 @pytest.mark.parametrize("L,J,group_size", [(16, (1.0, 0.5), 1), (16, (1.0, 0.6, -0.05, -0.1), 1),
                                             (12, (1.0, 0.5, 0.2), 2), (24, (1.0, 0.5), 1),
+                                            (24, (1.0, 0.6, -0.05, -0.1), 1),
                                             (3, (1.0,), 1), (4, (1.0, 0.5), 1), (4, (1.0, 0.6, -0.05, -0.1), 1),
                                             (6, (1.0, 0.5, 0.2), 1)])
 def test_running_energy_tracks_configuration_without_recompute(L, J, group_size):
