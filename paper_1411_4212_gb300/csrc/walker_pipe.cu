@@ -177,8 +177,8 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
   const int rep = a.st.perm[slot];
   const uint32_t omask = (uint32_t)a.own_mask;
 
-  // shared layout: ln g | H | offsets | J per slot | records[2][32] | owner table | spins
-  // (every section starts on a 16-byte boundary)
+  // shared layout: ln g | H | offsets | J per slot | records[2][32] | packed records[2][32] | owner
+  // table | lattice (in shared memory only); every section starts on a 16-byte boundary
   unsigned char* p = smem_raw;
   Lng* lng_s = reinterpret_cast<Lng*>(p);
   p += align16(sizeof(Lng) * (size_t)W);
@@ -192,8 +192,6 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
   p += sizeof(Rec<kTraj>) * 64;
   int4* pk = reinterpret_cast<int4*>(p);          // production: {dq lo, dq hi, ccur, ln u} per move
   p += sizeof(int4) * 64;
-  uint32_t* fhist = reinterpret_cast<uint32_t*>(p);  // production: energy fraction before each move of a block
-  p += sizeof(uint32_t) * 32;
   uint2* own = reinterpret_cast<uint2*>(p);
   p += sizeof(uint2) * ((size_t)omask + 1);
   Real* spin_s = reinterpret_cast<Real*>(p);
@@ -817,13 +815,14 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
         while (k < nvalid) {
           const uint32_t acc0 = acc_cur;
           uint32_t exc = 0, outb = 0;
+          uint32_t fh[8];   // fraction before each move of the block, for the restart
           int4 q[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) q[u] = P4[(k + u) & 31];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int kk = k + u;
-            if (lane == u) fhist[u] = frac;
+            fh[u] = frac;
             const uint32_t lo = (uint32_t)q[u].x;
             const int hi = q[u].y;
             const uint32_t cc = (uint32_t)q[u].z;
@@ -851,8 +850,9 @@ __device__ __forceinline__ void pipe_walk_slot(const WalkerArgs& a, const int sl
           n_rej += __popc(outb & ((exc & (0u - exc)) - 1u));
           // first exceptional move: the block's moves before it stand; restore the state there
           const int kx = __ffs(exc) - 1;
-          __syncwarp();
-          frac = fhist[kx - k];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (k + u == kx) frac = fh[u];
           acc_cur = acc0 | (acc_cur & ((1u << kx) - 1u));
           Efx = ((long long)bcur << 32) | frac;
           const int4 wx = P4[kx];
@@ -1042,7 +1042,7 @@ size_t walker_pipe_smem_bytes(bool traj, bool smem_lattice, int N, int W, int ow
   const size_t lng = align16((traj ? sizeof(double) : sizeof(long long)) * (size_t)W);
   const size_t h = align16((size_t)W * 4);
   const size_t real = traj ? sizeof(double) : sizeof(float);
-  const size_t recs = (traj ? sizeof(Rec<true>) : sizeof(Rec<false>)) * 64 + sizeof(int4) * 64 + sizeof(uint32_t) * 32;
+  const size_t recs = (traj ? sizeof(Rec<true>) : sizeof(Rec<false>)) * 64 + sizeof(int4) * 64;
   size_t bytes = lng + h + 4 * kMaxSlotsPerSite + real * kMaxSlotsPerSite + recs + 8 * (size_t)own_entries;
   if (smem_lattice) bytes += smem_site_bytes(traj) * (size_t)N;
   return bytes;
