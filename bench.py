@@ -72,6 +72,9 @@ def parse():
     p.add_argument("--target-lnf", type=float, default=1e-6, help="target: ln f_final of the plain and warm runs")
     p.add_argument("--target-replicas", type=int, default=2, help="target: plain and warm runs each")
     p.add_argument("--target-refs", type=int, default=1, help="target: reference runs (ln f_final / 10)")
+    p.add_argument("--target-seed-offset", type=int, default=0,
+                   help="target: first seed of the plain and warm runs past 8000 / 9000 (new runs against the "
+                        "same reference)")
     p.add_argument("--corpus-per-size", type=int, default=64, help="target: corpus runs per lattice size")
     p.add_argument("--mlp-cache", default=None,
                    help="target: .npz of the trained network; read when it exists (no corpus, no training), "
@@ -565,7 +568,7 @@ def run_target(args):
         refs.append(lng)
     ref = warmstart.reference_curve(refs)
     for r in range(args.target_replicas):
-        for kind, s0 in (("plain", 8000), ("warm", 9000)):
+        for kind, s0 in (("plain", 8000 + args.target_seed_offset), ("warm", 9000 + args.target_seed_offset)):
             rec, lng, pred = one(kind, s0 + r, lnf)
             rec["rms_vs_reference"] = warmstart.centred_rms(lng, ref)
             if pred is not None:
