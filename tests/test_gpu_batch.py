@@ -175,3 +175,38 @@ def test_batched_convergence_of_mixed_lattices_gives_every_job_its_result():
         peaks.append(tp)
         j.close()
     print("T_peak per job:", np.round(peaks, 3))
+
+
+def test_production_walk_does_not_depend_on_the_conflict_table_size():
+    """The conflict (owner) table maps a site to entry site mod size, so a smaller table flags more
+    pairs of moves that share an entry without sharing a neighbourhood; the resolver drops those
+    aliases before they become events.  The walk must not depend on the table size: a four-shell
+    bcc L = 24 lattice (in global memory) run alone (2048 entries) and as a one-job batch with 256,
+    1024 and 8192 entries reaches the same state bit for bit."""
+    spec = dict(L=24, J=(1.0, 0.6, -0.05, -0.1), n_bins=2000, n_windows=8, walkers_per_window=2)
+    states, recomputes = [], []
+    for cap in (None, 256, 1024, 8192):
+        g = rw.REWL(kind=rw.BCC, mode=rw.PRODUCTION, lnf_final=1e-8, seed=5, exchange_interval=5000,
+                    recompute_every=1000, group_size=1, **spec)
+        assert g.info()["pipelined"] == 1 and g.info()["lattice_in_shared"] == 0
+        if cap is None:
+            g.init_walkers()
+            g.run_intervals(3, stats=False)
+        else:
+            with rw.Batch([g]) as b:
+                b.set_tuning(1, 0, cap)
+                assert b.info()["n_smem_lattice_jobs"] == 0
+                b.run_intervals(3)
+        w = g.walkers()
+        st = {k: np.array(w[k]) for k in ("H", "bin", "replica", "accepts", "steps", "stage")}
+        for k in ("lng", "E", "lnf"):
+            st[k] = np.array(w[k]).view(np.int64)
+        st["spins"] = g.spins().view(np.int64)
+        states.append(st)
+        recomputes.append(g.counters()["recomputes"])
+        g.close()
+    print("corrections (real conflicts only):", recomputes)
+    assert len(set(recomputes)) == 1     # aliases are dropped, so only real conflicts are corrected
+    for st in states[1:]:
+        for k in st:
+            assert np.array_equal(states[0][k], st[k]), k
