@@ -1,6 +1,6 @@
-"""The window-partition protocol on CPU: two gloo ranks on 127.0.0.1 drive the round protocol of
+"""The window-partition protocol on CPU: two or three gloo ranks on 127.0.0.1 drive the round protocol of
 paper_1411_4212_gb300.partition (bins by max all-reduce, ln g lookups by sum all-reduce, the decision,
-slot states moved by all-reduce, the second look) across the two halves of a REWL run.  Each rank holds
+slot states moved by all-reduce, the second look) across contiguous window ranges of a REWL run.  Each rank holds
 a stand-in part that keeps its slot states and configurations in plain arrays.  The arithmetic of the
 decision is Eq. 5 with the oracle's Philox and exp, as the library's exchange kernel does it.
 
@@ -13,6 +13,7 @@ import socket
 import sys
 
 import numpy as np
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CFG = dict(L=4, J=(1.0, 0.5), e_min=-400.0, e_max=0.0, n_bins=120, n_windows=6, walkers_per_window=3,
@@ -20,9 +21,9 @@ CFG = dict(L=4, J=(1.0, 0.5), e_min=-400.0, e_max=0.0, n_bins=120, n_windows=6, 
 WARM_INTERVALS, ROUNDS = 12, 16
 
 
-def _oracle_state():
+def _oracle_state(n_windows):
     import oracle
-    o = oracle.OracleREWL(kind=oracle.BCC, **CFG)
+    o = oracle.OracleREWL(kind=oracle.BCC, **dict(CFG, n_windows=n_windows))
     o.init_walkers()
     o.run_intervals(WARM_INTERVALS)
     return o
@@ -136,15 +137,15 @@ class OraclePart:
                 "replica": (self.conf - self.window_begin * self.m).astype(np.int32)}
 
 
-def _rank(rank, port, q):
-    os.environ.update(RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+def _rank(rank, world, n_windows, port, q):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
                       MASTER_PORT=str(port))
     sys.path.insert(0, ROOT)
     import torch.distributed as dist
     from paper_1411_4212_gb300.partition import DistComm, PartitionedRun, window_ranges
     dist.init_process_group("gloo")
-    k0, k1 = window_ranges(CFG["n_windows"], 2)[rank]
-    part = OraclePart(_oracle_state(), k0, k1)
+    k0, k1 = window_ranges(n_windows, world)[rank]
+    part = OraclePart(_oracle_state(n_windows), k0, k1)
     run = PartitionedRun([part], DistComm())
     for _ in range(ROUNDS):
         run.exchange_round()
@@ -164,19 +165,21 @@ def _free_port():
     return port
 
 
-def test_two_gloo_ranks_exchange_like_one_process():
+@pytest.mark.parametrize("world,n_windows", [(2, 6), (3, 7)])
+def test_gloo_ranks_exchange_like_one_process(world, n_windows):
+    """Two ranks with three windows each, and three ranks with 3, 2 and 2 windows (uneven ranges)."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank, args=(r, world, n_windows, port, q)) for r in range(world)]
     for p in procs:
         p.start()
-    res = sorted((q.get(timeout=300) for _ in range(2)), key=lambda x: x[0])
+    res = sorted((q.get(timeout=300) for _ in range(world)), key=lambda x: x[0])
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
     sys.path.insert(0, ROOT)
-    o = _oracle_state()
+    o = _oracle_state(n_windows)
     a0, b0 = o.exchange_counts()
     for _ in range(ROUNDS):
         o.exchange()
@@ -188,5 +191,5 @@ def test_two_gloo_ranks_exchange_like_one_process():
         assert np.array_equal(g["bin"], w["bin"]), rank
         assert np.array_equal(g["lng"].view(np.int64), w["lng"].view(np.int64)), rank
         assert np.array_equal(att, a1 - a0) and np.array_equal(acc, b1 - b0), rank
-    assert res[0][4] + res[1][4] > 0, "no slot state crossed the ranks"
+    assert sum(r[4] for r in res) > 0, "no slot state crossed the ranks"
     assert int((b1 - b0).sum()) > 0
