@@ -152,8 +152,12 @@ typedef struct {
 typedef struct {
   int64_t moves;
   int64_t accepts;
-  int64_t recomputes;          /* trial moves whose dE was re-evaluated after an earlier accepted
-                                  move in the same batch touched its neighbourhood */
+  int64_t recomputes;          /* trial moves whose dE was re-evaluated or corrected after an accepted
+                                  move still in flight (the walker's batch or the one before) touched
+                                  its neighbourhood.  The production walker over a lattice in global
+                                  memory counts real conflicts only; with the lattice in shared
+                                  memory, moves sharing a conflict-table entry count too (the table
+                                  has an entry per site up to 8192 sites) */
   int64_t batches_scan;        /* production, warp-specialised walker: batches of 32 moves resolved */
   int64_t batches_blocks;      /*   by the warp scan, by 8-move blocks and one move at a time */
   int64_t batches_sequential;  /*   (all 0 for the other walkers and in trajectory mode) */
