@@ -309,17 +309,42 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # DRAM traffic of the walker kernel, taken from the committed ncu summary of the same kernel (the
 # summary under profiles/ whose `kernel` field names it).  The summary records a hash of the
-# kernel's sources; once they change the figure no longer applies and the traffic is reported as null.
+# kernel's sources (code only, without comments); once the code changes the figure no longer applies
+# and the traffic is reported as null.
 PROFILES = os.path.join(ROOT, "profiles")
 KERNEL_SOURCES = ["walker_pipe.cu", "walker_common.cuh", "device_common.cuh", "rewl_types.h"]
 
 
+def _code_only(text):
+    """C++ source without comments and with whitespace runs collapsed: what the compiler sees."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"' or c == "'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash():
+    """Hash of the walker kernel's sources, comments and layout excluded."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1411_4212_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1411_4212_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()
 
 

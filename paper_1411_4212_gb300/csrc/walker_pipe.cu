@@ -4,16 +4,19 @@
 // One CTA per walker slot.  Warp 1 (producer) prepares batch b+1 of 32 trial moves while warp 0
 // (resolver) resolves batch b strictly in order, so the walk is the sequential Markov chain:
 //   producer: Philox draws, the local field h_i = sum_j J_ij S_j over the coupling shells (bcc
-//     offsets known at compile time, all neighbour loads issued at once), dE = -(S'-S).h, and two
-//     conflict masks read from a shared-memory owner table -- the moves of batch b (still being
+//     offsets known at compile time, the neighbour loads in one unrolled loop), dE = -(S'-S).h, and
+//     two conflict masks read from a shared-memory owner table -- the moves of batch b (still being
 //     resolved while batch b+1 reads the lattice) and the earlier moves of batch b+1 that sit on the
 //     same site or a neighbouring one;
-//   resolver: a move whose mask meets a move accepted since the lattice was read is re-evaluated on
-//     the current lattice; then accept with min[1, g(E)/g(E')] (reject outside the window) and add
-//     ln f to ln g and 1 to H at the resulting state.
-// The owner table may alias sites (hashed) -- an alias only causes an exact re-evaluation.  Two
-// record buffers alternate; named barriers READY(b mod 2) and DONE(b mod 2) order the hand-over, so
-// the producer reads the lattice only after every move of batch b-1 has been written.
+//   resolver: a move whose mask meets a move accepted since the lattice was read is corrected
+//     exactly (production: from the move records; trajectory: re-evaluated on the current lattice);
+//     then accept with min[1, g(E)/g(E')] (reject outside the window) and add ln f to ln g and 1 to
+//     H at the resulting state.
+// The owner table may alias sites (hashed): an alias names a move that cannot change the field, so
+// its correction changes nothing, and the production walker over a global lattice drops it before
+// it becomes an event.  Two record buffers alternate; named barriers READY(b mod 2) and DONE(b mod 2)
+// order the hand-over, so the producer reads the lattice only after every move of batch b-1 has been
+// written.
 #include <cstring>
 
 #include "walker_common.cuh"
