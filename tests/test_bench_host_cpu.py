@@ -1,6 +1,7 @@
 """Host logic of bench.py's roofline (no GPU): the committed ncu summaries name kernels that exist
 in the sources and carry figures that parse; the DRAM traffic is scaled to a launch by its moves
-and dropped once the kernel's sources no longer hash to the profiled ones."""
+and dropped once the kernel's sources (code only, without comments) no longer hash to the profiled
+ones."""
 import os
 import re
 
@@ -61,3 +62,13 @@ def test_hbm_peak_reads_the_measured_file_or_falls_back(tmp_path, monkeypatch):
     (tmp_path / "MEASURED_PEAKS.json").unlink()
     peak, src = bench.hbm_peak()
     assert peak == pytest.approx(6.8e12) and "fallback" in src
+
+
+def test_source_hash_covers_code_not_comments():
+    code = 'int f(int x) {\n  return x + 1;  // one more\n}\n/* block\n comment */ const char* s = "a // b";\n'
+    same = 'int f(int x) { return x + 1; }\n  const char* s = "a // b";  // another comment\n'
+    other = 'int f(int x) {\n  return x + 2;\n}\nconst char* s = "a // b";\n'
+    assert bench._code_only(code) == bench._code_only(same)
+    assert bench._code_only(code) != bench._code_only(other)
+    assert '"a // b"' in bench._code_only(code)               # string literals are code
+    assert "'//'" in bench._code_only("char c = '//';")       # and so are character literals
